@@ -1,0 +1,463 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form printed in (or following directly from) the paper, a textbook special
+case, a library routine applied to an independent formulation, brute-force
+integration, an invariant the method guarantees, or a value the paper prints.
+A plausible slip anywhere in the oracle (a dropped term, a wrong sign or
+index, a transposed operand) fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.integrate as si
+import scipy.linalg as sl
+
+import oracle
+import workloads as W
+
+HBAR = 6.62607015e-34 / (2 * math.pi)
+DT = W.DZ_SIT / W.C0
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rand_herm(rng, n, scale=1.0):
+    a = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    return scale * (a + a.conj().T) / 2
+
+
+def rand_rho(rng, n):
+    a = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    r = a @ a.conj().T
+    return r / np.trace(r).real
+
+
+# ----------------------------------------------------------------- expm
+def test_expm_closed_forms():
+    th = 0.7
+    g = np.array([[0, -th], [th, 0]], complex)
+    np.testing.assert_allclose(oracle.expm(g), [[math.cos(th), -math.sin(th)],
+                                                [math.sin(th), math.cos(th)]], atol=1e-15)
+    d = np.diag([0.3, -2.0, 1j * 4.0])
+    np.testing.assert_allclose(oracle.expm(d), np.diag(np.exp(np.diag(d))), atol=1e-14)
+    nil = np.array([[0, 1, 0], [0, 0, 1], [0, 0, 0]], complex) * 2.5
+    np.testing.assert_allclose(oracle.expm(nil), np.eye(3) + nil + nil @ nil / 2, atol=1e-14)
+
+
+@pytest.mark.parametrize("n,scale", [(4, 0.1), (9, 3.0), (16, 40.0), (36, 1.0)])
+def test_expm_vs_scipy(n, scale):
+    rng = np.random.default_rng(n)
+    a = scale * (rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))) / math.sqrt(n)
+    ref = sl.expm(a)
+    np.testing.assert_allclose(oracle.expm(a), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+# ----------------------------------------------------------------- eigh
+def test_eigh_pauli_x():
+    w, v = oracle.eigh(np.array([[0, 1], [1, 0]], complex))
+    assert sorted(w) == pytest.approx([-1.0, 1.0], abs=1e-15)
+    for k in range(2):
+        np.testing.assert_allclose(np.array([[0, 1], [1, 0]]) @ v[:, k], w[k] * v[:, k], atol=1e-15)
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 6])
+def test_eigh_random(n):
+    rng = np.random.default_rng(10 + n)
+    a = rand_herm(rng, n)
+    w, v = oracle.eigh(a)
+    np.testing.assert_allclose(np.sort(w), np.linalg.eigvalsh(a), atol=1e-13)
+    np.testing.assert_allclose(v.conj().T @ v, np.eye(n), atol=1e-13)
+    np.testing.assert_allclose(v @ np.diag(w) @ v.conj().T, a, atol=1e-13)
+
+
+def test_eigh_degenerate():
+    q, _ = np.linalg.qr(np.random.default_rng(3).normal(size=(4, 4)))
+    a = q @ np.diag([1.0, 1.0, -2.0, 0.5]) @ q.T
+    w, v = oracle.eigh(a.astype(complex))
+    np.testing.assert_allclose(np.sort(w), [-2.0, 0.5, 1.0, 1.0], atol=1e-13)
+    np.testing.assert_allclose(v @ np.diag(w) @ v.conj().T, a, atol=1e-13)
+
+
+# ----------------------------------------------------------- Liouvillian
+def _qm3(rng, with_rate_form=False):
+    n = 3
+    h0 = np.diag([0.0, 1.0e-20, 1.7e-20]).astype(complex)
+    h0[0, 1], h0[1, 0] = 2e-21 + 1.5e-21j, 2e-21 - 1.5e-21j
+    h0[1, 2], h0[2, 1] = -1e-21j, 1e-21j
+    mu = rand_herm(rng, n, 1e-29)
+    ops = [np.outer(np.eye(n)[i], np.eye(n)[j]).astype(complex) for i, j in [(0, 2), (1, 2), (0, 1)]]
+    return W.QM(n, 1e24, h0, mu, rand_rho(rng, n), np.array([3e11, 1e11, 2e10]), np.array(ops))
+
+
+def test_liouvillian_preserves_trace_and_hermiticity():
+    rng = np.random.default_rng(1)
+    qm = _qm3(rng)
+    qm.scattering = np.array([[0, 1e10, 2e10], [5e9, 0, 0], [0, 7e9, 0]])
+    qm.pure_dephasing = np.array([1e11, 2e11, 3e11])
+    L = oracle.liouvillian(qm)
+    n = 3
+    for _ in range(3):
+        rho = rand_herm(rng, n)
+        d = (L @ rho.reshape(-1)).reshape(n, n)
+        assert abs(np.trace(d)) < 1e-12 * np.abs(d).max()
+        np.testing.assert_allclose(d, d.conj().T, atol=1e-12 * np.abs(d).max())
+
+
+def test_liouvillian_matches_master_equation_products():
+    """L0 vec(rho) equals -i/hbar [H0, rho] + sum g (L rho L^+ - 1/2{L^+L, rho})
+    written with matrix products (Eq. master, Eq. lindbladdiss)."""
+    rng = np.random.default_rng(2)
+    qm = _qm3(rng)
+    L = oracle.liouvillian(qm)
+    rho = rand_herm(rng, 3)
+    ref = -1j / HBAR * (qm.h0 @ rho - rho @ qm.h0)
+    for g, op in zip(qm.lindblad_rates, qm.lindblad_ops):
+        ll = op.conj().T @ op
+        ref += g * (op @ rho @ op.conj().T - 0.5 * (ll @ rho + rho @ ll))
+    np.testing.assert_allclose((L @ rho.reshape(-1)).reshape(3, 3), ref, atol=1e-10 * np.abs(ref).max())
+
+
+def test_rate_form_equals_equivalent_operators():
+    """The rate form (Eq. relax_pop + the dephasing law) equals the explicit
+    operators |i><j| at rate gamma_ij plus |k><k| at rate g_k, whose pure
+    dephasing is (g_i + g_j)/2 per pair."""
+    n = 3
+    R = np.array([[0, 1e10, 2e10], [5e9, 0, 3e9], [0, 7e9, 0]])
+    gk = np.array([1e11, 4e11, 2.5e11])
+    deph = np.array([(gk[0] + gk[1]) / 2, (gk[0] + gk[2]) / 2, (gk[1] + gk[2]) / 2])  # 12, 13, 23
+    h0 = np.diag([0.0, 1e-20, 2e-20]).astype(complex)
+    mu = np.zeros((n, n), complex)
+    rho = np.diag([1.0, 0, 0]).astype(complex)
+    qa = W.QM(n, 1.0, h0, mu, rho, scattering=R, pure_dephasing=deph)
+    ops, rates = [], []
+    for i in range(n):
+        for j in range(n):
+            if i != j and R[i, j] > 0:
+                ops.append(np.outer(np.eye(n)[i], np.eye(n)[j]).astype(complex))
+                rates.append(R[i, j])
+    for k in range(n):
+        ops.append(np.outer(np.eye(n)[k], np.eye(n)[k]).astype(complex))
+        rates.append(gk[k])
+    qb = W.QM(n, 1.0, h0, mu, rho, np.array(rates), np.array(ops))
+    np.testing.assert_allclose(oracle.liouvillian(qa), oracle.liouvillian(qb), atol=1e-6)
+
+
+def test_two_level_bloch_equations():
+    """qm_desc_2lvl parameters reproduce the optical Bloch equations of
+    Sec. 3.1.1: d rho21 = -(i w21 + g2) rho21, d w = -g1 (w - w0)."""
+    w21, g1, g2, w0 = 2e14, 3e11, 7e11, -0.4
+    qm = W.qm_two_level(1e24, w21, 1e-29, g1, g2, w0)
+    L = oracle.liouvillian(qm)
+    rho = np.array([[0.6, 0.2 - 0.1j], [0.2 + 0.1j, 0.4]])
+    d = (L @ rho.reshape(-1)).reshape(2, 2)
+    assert d[1, 0] == pytest.approx(-(1j * w21 + g2) * rho[1, 0], rel=1e-12)
+    w = rho[1, 1] - rho[0, 0]
+    assert (d[1, 1] - d[0, 0]).real == pytest.approx(-g1 * (w - w0), rel=1e-12)
+
+
+# ------------------------------------------------------- single-cell pins
+def test_free_evolution_closed_form():
+    """E = 0: rho21(t) = rho21(0) e^{-(i w21 + g2) t}, w(t) = w0 + (w(0) - w0)
+    e^{-g1 t}, and d_t P = 2 n3D Re(mu12 d rho21/dt) (Sec. 3.1.1, Sec. 2)."""
+    w21, g1, g2, w0, dens, d = 2e14, 1e12, 3e12, -0.6, 1e24, 1e-29
+    rho0 = np.array([[0.7, 0.3 + 0.2j], [0.3 - 0.2j, 0.3]])
+    qm = W.qm_two_level(dens, w21, d, g1, g2, w0, rho_init=rho0)
+    nt = 3000
+    traj, pd = oracle.cell_evolve(qm, DT, np.zeros(nt), want_pdot=True)
+    t = (np.arange(nt) + 1) * DT
+    r21 = rho0[1, 0] * np.exp(-(1j * w21 + g2) * t)
+    np.testing.assert_allclose(traj[:, 1, 0], r21, rtol=0, atol=1e-13)
+    wt = w0 + ((rho0[1, 1] - rho0[0, 0]).real - w0) * np.exp(-g1 * t)
+    np.testing.assert_allclose((traj[:, 1, 1] - traj[:, 0, 0]).real, wt, atol=1e-13)
+    mu12 = qm.mu[0, 1]
+    pd_ref = 2 * dens * np.real(mu12 * (-(1j * w21 + g2)) * r21)
+    np.testing.assert_allclose(pd, pd_ref, rtol=0, atol=1e-11 * np.abs(pd_ref).max())
+
+
+def test_polarisation_current_complex_dipole():
+    """d_t P = n3D tr{mu d_t rho} (Sec. 2) for a complex dipole operator and
+    non-diagonal H0, with d_t rho from the master equation in matrix-product
+    form evaluated on the oracle's own rho^{n+1/2}."""
+    rng = np.random.default_rng(5)
+    qm = _qm3(rng)
+    e = 2e9 * np.sin(np.arange(200) * 0.05)
+    traj, pd = oracle.cell_evolve(qm, DT, e, want_pdot=True)
+    for k in (0, 57, 199):
+        rho = traj[k]
+        H = qm.h0 - qm.mu * e[k]
+        d = -1j / HBAR * (H @ rho - rho @ H)
+        for g, op in zip(qm.lindblad_rates, qm.lindblad_ops):
+            ll = op.conj().T @ op
+            d += g * (op @ rho @ op.conj().T - 0.5 * (ll @ rho + rho @ ll))
+        ref = qm.density * np.trace(qm.mu @ d).real
+        assert pd[k] == pytest.approx(ref, rel=1e-9)
+
+
+def test_population_relaxation_matrix():
+    """Diagonal H0, rate form: populations follow expm(G t) p0 with
+    G_ij = gamma_ij, G_jj = -sum_{i != j} gamma_ij (Eq. relax_pop)."""
+    n = 4
+    R = np.array([[0, 2e11, 0, 1e11], [0, 0, 3e11, 0], [5e10, 0, 0, 4e11], [0, 1e11, 0, 0]], float)
+    G = R.copy()
+    np.fill_diagonal(G, -R.sum(axis=0))
+    p0 = np.array([0.1, 0.2, 0.3, 0.4])
+    qm = W.QM(n, 1.0, np.diag([0, 1e-20, 2e-20, 3e-20]).astype(complex), np.zeros((n, n), complex),
+              np.diag(p0).astype(complex), scattering=R, pure_dephasing=np.zeros(6))
+    nt = 800
+    traj = oracle.cell_evolve(qm, DT, np.zeros(nt))
+    for k in (0, 99, 799):
+        ref = sl.expm(G * (k + 1) * DT) @ p0
+        np.testing.assert_allclose(np.diag(traj[k]).real, ref, atol=1e-14)
+
+
+def test_dephasing_law():
+    """Coherences decay at (tau_i^-1 + tau_j^-1)/2 + gamma_ij,p."""
+    n = 3
+    R = np.array([[0, 2e11, 1e11], [0, 0, 3e11], [5e10, 0, 0]])
+    deph = np.array([1e11, 4e11, 2e11])   # 12, 13, 23
+    inv_tau = R.sum(axis=0)
+    rho0 = np.full((n, n), 0.1, complex) + np.diag([0.2, 0.2, 0.2])
+    h0 = np.diag([0, 1e-20, 2.5e-20]).astype(complex)
+    qm = W.QM(n, 1.0, h0, np.zeros((n, n), complex), rho0, scattering=R, pure_dephasing=deph)
+    nt = 500
+    traj = oracle.cell_evolve(qm, DT, np.zeros(nt))
+    t = nt * DT
+    for (i, j), gp in zip([(0, 1), (0, 2), (1, 2)], deph):
+        rate = 0.5 * (inv_tau[i] + inv_tau[j]) + gp
+        w = (h0[i, i] - h0[j, j]).real / HBAR
+        assert traj[-1, i, j] == pytest.approx(rho0[i, j] * np.exp((-1j * w - rate) * t), rel=1e-12)
+
+
+def _dc_rabi_error(e, dt, t_end):
+    w0, d = 2e14, 1e-29
+    qm = W.qm_two_level(1.0, w0, d, 0.0, 0.0, -1.0)
+    qm.scattering = np.zeros((2, 2))
+    qm.pure_dephasing = np.zeros(1)
+    nt = int(round(t_end / dt))
+    traj = oracle.cell_evolve(qm, dt, np.full(nt, e))
+    H = qm.h0 - qm.mu * e
+    errs = []
+    for k in range(nt):
+        U = sl.expm(-1j * H * (k + 1) * dt / HBAR)
+        ref = U @ qm.rho_init @ U.conj().T
+        errs.append(np.abs(traj[k] - ref).max())
+    t = (np.arange(nt) + 1) * dt
+    ox = 2 * d * e / HBAR
+    om = math.hypot(w0, ox)
+    np.testing.assert_allclose(traj[:, 1, 1].real, ref_p22(ox, om, t), atol=max(errs) * 1.01 + 1e-15)
+    return max(errs)
+
+
+def ref_p22(ox, om, t):
+    return (ox / om) ** 2 * np.sin(om * t / 2) ** 2
+
+
+def test_dc_rabi_second_order():
+    """Constant E, no relaxation: exact rho(t) = e^{-iHt/hbar} rho0 e^{iHt/hbar}
+    with H = H0 - mu E; rho22 is the textbook Rabi formula.  The split step
+    converges at order 2 (Strang): halving dt cuts the error 4x."""
+    e = 3e9
+    t_end = 400 * DT
+    e1 = _dc_rabi_error(e, DT, t_end)
+    e2 = _dc_rabi_error(e, DT / 2, t_end)
+    assert e1 < 1e-2
+    assert 3.6 < e1 / e2 < 4.4
+
+
+def test_split_step_converges_to_master_equation():
+    """Brute force: a random 3-level cell with relaxation under a
+    piecewise-constant field, integrated by RK45 at tight tolerance from the
+    master equation written with matrix products; the split step's error
+    falls at order 2."""
+    rng = np.random.default_rng(7)
+    qm = _qm3(rng)
+    n = 3
+
+    def rhs(t, y, e):
+        rho = y.reshape(n, n)
+        H = qm.h0 - qm.mu * e
+        d = -1j / HBAR * (H @ rho - rho @ H)
+        for g, op in zip(qm.lindblad_rates, qm.lindblad_ops):
+            ll = op.conj().T @ op
+            d += g * (op @ rho @ op.conj().T - 0.5 * (ll @ rho + rho @ ll))
+        return d.reshape(-1)
+
+    def err(dt, t_end=150 * DT):
+        nt = int(round(t_end / dt))
+        tc = np.arange(nt) * dt
+        e = 3e9 * np.sin(2.3e14 * tc) / np.cosh((tc - 0.5 * t_end) / (0.2 * t_end))
+        traj = oracle.cell_evolve(qm, dt, e)
+        y = qm.rho_init.reshape(-1).astype(complex)
+        errs = []
+        for k in range(nt):
+            sol = si.solve_ivp(rhs, (0, dt), y, args=(e[k],), method="DOP853", rtol=1e-13, atol=1e-15)
+            y = sol.y[:, -1]
+            errs.append(np.abs(traj[k] - y.reshape(n, n)).max())
+        return max(errs)
+
+    e1, e2 = err(DT), err(DT / 2)
+    assert e1 < 1e-3
+    assert 3.5 < e1 / e2 < 4.5
+
+
+def test_resonant_pi_and_2pi_pulses():
+    """A long resonant sech of area pi inverts a two-level cell, area 2 pi
+    returns it (paper Sec. 4.1: pi / 2pi pulses invert once / twice); the
+    residue is bounded by the rotating-wave error O(1/(w0 tau))."""
+    w0, d, tau = 2 * math.pi * 2e14, 1e-29, 100e-15
+    qm = W.qm_two_level(1.0, w0, d, 0.0, 0.0, -1.0)
+    qm.scattering = np.zeros((2, 2))
+    qm.pure_dephasing = np.zeros(1)
+    dt = DT
+    nt = int(16 * tau / dt)
+    t = np.arange(nt) * dt
+    for area, final in [(math.pi, 1.0), (2 * math.pi, 0.0)]:
+        e0 = W.sech_area_amplitude(area, d, tau)
+        e = e0 / np.cosh((t - 8 * tau) / tau) * np.sin(w0 * t)
+        traj = oracle.cell_evolve(qm, dt, e)
+        assert traj[-1, 1, 1].real == pytest.approx(final, abs=0.02)
+        if area > 4:
+            assert traj[:, 1, 1].real.max() > 0.98
+
+
+# ---------------------------------------------------------- full-sweep pins
+def _vacuum(n_cells=2048, t_end=2e-12, far_t0=True):
+    p = W.sit_2lvl(n_cells=n_cells, t_end=t_end)
+    p.qms[0].density = 0.0
+    if far_t0:
+        p.sources[0].t0 = 30 * p.sources[0].tau
+    return p
+
+
+def test_vacuum_translation_exact():
+    """Courant number 1 in vacuum: the injected pulse arrives at cell m
+    unchanged, E_m^{n+1} = S(t_{n+1} - (m - m_s) dt); nothing leaks into the
+    scattered-field cells and the first-order Mur ends reflect nothing."""
+    p = _vacuum()
+    cells = [2, 3, 100, 1024, 2046, 2047]
+    p.probes = [W.Probe(c, W.Q_E) for c in cells] + [W.Probe(0, W.Q_E), W.Probe(1, W.Q_E)]
+    r = oracle.run(p)
+    n = np.arange(r["nt"])
+    s = p.sources[0]
+    for k, c in enumerate(cells):
+        a = n + 1 - (c - 2)
+        ref = np.where(a >= 0, s.waveform(a * r["dt"]), 0.0)
+        assert np.abs(r["records"][k] - ref).max() <= 1e-13 * s.e0
+    assert np.abs(r["records"][-2:]).max() <= 1e-13 * s.e0
+
+
+def test_pec_reflection_exact():
+    """R = 1: the right end reflects the pulse with E -> -E about the last
+    cell centre."""
+    p = _vacuum()
+    p.refl_right = 1.0
+    cells = [2, 500, 1500, 2040]
+    p.probes = [W.Probe(c, W.Q_E) for c in cells]
+    r = oracle.run(p)
+    n = np.arange(r["nt"])
+    s = p.sources[0]
+    for k, c in enumerate(cells):
+        a = n + 1 - (c - 2)
+        b = n + 1 - (2 * 2047 - c - 2)
+        ref = np.where(a >= 0, s.waveform(a * r["dt"]), 0.0) - np.where(b >= 0, s.waveform(b * r["dt"]), 0.0)
+        assert np.abs(r["records"][k] - ref).max() <= 1e-13 * s.e0
+
+
+def test_left_going_source_exact():
+    p = _vacuum()
+    s = p.sources[0]
+    s.kind, s.cell = W.SRC_TFSF_LEFT, 2045
+    cells = [2045, 1000, 3, 2046, 2047]
+    p.probes = [W.Probe(c, W.Q_E) for c in cells]
+    r = oracle.run(p)
+    n = np.arange(r["nt"])
+    for k, c in enumerate(cells[:3]):
+        a = n + 1 - (2045 - c)
+        ref = np.where(a >= 0, s.waveform(a * r["dt"]), 0.0)
+        assert np.abs(r["records"][k] - ref).max() <= 1e-13 * s.e0
+    assert np.abs(r["records"][3:]).max() <= 1e-13 * s.e0
+
+
+def test_invariants_along_sweep():
+    """Each splitting factor is completely positive and trace preserving,
+    so rho stays a density matrix (Sec. 2.2): trace 1, Hermitian, PSD."""
+    p = W.sit_2lvl(n_cells=256, t_end=0.0, n_steps=600)
+    p.qms[0].rho_init = np.array([[0.8, 0.3], [0.3, 0.2]], complex)
+    bound = 2e-15 * 600          # rounding, accumulated step by step
+    r = oracle.run(p, check_invariants=True)
+    tr, herm, mn = r["stats"]
+    assert tr < bound and herm < bound and mn > -bound
+    p3 = W.lambda_3lvl(n_cells=256, n_steps=600, tau=10e-15, t0=60e-15)
+    r = oracle.run(p3, check_invariants=True)
+    tr, herm, mn = r["stats"]
+    assert tr < bound and herm < bound and mn > -bound
+
+
+def test_beer_law_small_signal():
+    """A weak pulse through the two-level slab: ln|E_out/E_in|(w) equals
+    -Im[(w/c)(sqrt(1+chi) - 1)] L_med with the two-pole Lorentzian
+    chi(w) = (n3D d^2 / eps0 hbar)[1/(w0 - w - i g2) + 1/(w0 + w + i g2)]."""
+    d, w0, g2, dens = 1e-29, 2e14, 1e13, 1e24
+    p = W.sit_2lvl(t_end=2e-12, pulse_area=0.01 * math.pi, gamma1=1e9, gamma2=g2)
+    m_out = 2000
+    p.probes = [W.Probe(m_out, W.Q_E)]
+    r = oracle.run(p)
+    dt, nt = r["dt"], r["nt"]
+    n = np.arange(nt)
+    a = n + 1 - (m_out - 2)
+    e_in = np.where(a >= 0, p.sources[0].waveform(a * dt), 0.0)
+    e_out = r["records"][0]
+    nf = 8 * nt
+    f_in, f_out = np.fft.rfft(e_in, nf), np.fft.rfft(e_out, nf)
+    w = 2 * np.pi * np.fft.rfftfreq(nf, dt)
+    sel = np.abs(w - w0) < 3 * g2
+    eps0 = 8.8541878128e-12
+    chi = dens * d * d / (eps0 * HBAR) * (1 / (w0 - w - 1j * g2) + 1 / (w0 + w + 1j * g2))
+    l_med = 1844 * p.dz
+    pred = -np.imag(w / W.C0 * (np.sqrt(1 + chi) - 1)) * l_med
+    meas = np.log(np.abs(f_out[sel] / f_in[sel]))
+    peak = np.abs(pred[sel]).max()
+    assert 0.4 < peak < 0.6
+    assert np.abs(meas - pred[sel]).max() <= 0.02 * peak
+
+
+def test_sit_front_cell_inversions():
+    """2 pi pulse: the first medium cell is inverted and returned to the
+    ground state; a pi pulse leaves it inverted (Sec. 4.1)."""
+    tau, w0 = 100e-15, 2 * math.pi * 2e14
+    for area, final11 in [(2 * math.pi, 1.0), (math.pi, 0.0)]:
+        p = W.sit_2lvl(n_cells=300, t_end=2.2e-12, pulse_area=area, omega0=w0, tau=tau, t0=800e-15)
+        p.regions = [W.Region(0, 0.0, 150.5 * p.dz), W.Region(1, 150.5 * p.dz, p.length)]
+        p.probes = [W.Probe(151, W.Q_RHO_RE, 0, 0)]
+        r = oracle.run(p)
+        rho11 = r["records"][0]
+        assert rho11[-1] == pytest.approx(final11, abs=0.05)
+        if area > 4:
+            assert rho11.min() < 0.05
+
+
+# -------------------------------------------------------------- golden
+def test_golden_sit_listing_pulse_area():
+    """The SIT listing prints the sech amplitude 4.2186e9 V/m for 1/tau =
+    2e14 1/s and z21 = 6.24e-11 m: its pulse area e z21 E0 pi tau / hbar is
+    2 pi to 2e-4 (the printed inputs agree to four significant digits),
+    which pins hbar and e."""
+    g = json.load(open(os.path.join(GOLDEN, "sit_listing.json")))
+    e = 1.602176634e-19
+    d = e * g["z21"]
+    tau = 1.0 / g["sech_inv_tau"]
+    area = d * g["sech_amplitude"] * math.pi * tau / HBAR
+    assert area / math.pi == pytest.approx(g["expected_pulse_area_over_pi"], rel=g["agreement_rel"])
+    # the oracle's two-level cell, driven by that pulse on resonance with the
+    # listing's parameters, is inverted near the pulse centre (area 2 pi,
+    # few-cycle so only approximately)
+    qm = W.qm_two_level(g["density"], g["omega21"], d, g["gamma1"], g["gamma2"], g["w0"])
+    nt = int(40 * tau / DT)
+    t = np.arange(nt) * DT
+    t0 = g["sech_t0_over_tau"] * tau
+    field = g["sech_amplitude"] / np.cosh((t - t0) / tau) * np.sin(2 * math.pi * g["sech_frequency_hz"] * t)
+    traj = oracle.cell_evolve(qm, DT, field)
+    assert traj[:, 1, 1].real.max() > 0.8
