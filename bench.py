@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the 1D Maxwell-Bloch hot path on GB300.
+
+Workload (one bench step = one whole simulation): the two-level SIT medium at
+scale -- 1,048,576 cells, 200,000 time steps, +-1 % seeded per-cell jitter of
+density and transition frequency -- solved through the C ABI.  Metric:
+Gcell-steps/s (cells x time steps / device time).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own replica of the workload (the path does
+not need any exchange between GPUs); value = all ranks' cell-steps / the
+slowest rank's time.  --impl reference times the CPU FP64 oracle on bounded
+samples of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "Gcell-steps/s"
+HBM_FALLBACK = 6800.0
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(name):
+    if name == "sit_2lvl_jitter":
+        return W.sit_2lvl_jitter()
+    if name == "sit_2lvl_jitter_small":
+        return W.sit_2lvl_jitter(n_cells=65_536, n_steps=20_000)
+    return W.WORKLOADS[name]()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_sample(p, cells, steps):
+    """A slab of the workload for timing the oracle: `cells` consecutive
+    medium cells (with their jitter) driven by the same source."""
+    m0 = int(math.ceil(0.05 * p.n_cells))
+    jit = None if p.jitter is None else p.jitter[m0:m0 + cells].copy()
+    length = cells * p.dz
+    return p.replace(n_cells=cells, length=length, regions=[W.Region(1, 0.0, length)], jitter=jit,
+                     n_steps=steps, t_end=0.0, probes=[W.Probe(cells // 2, W.Q_E)],
+                     sources=[W.Source(W.SRC_TFSF_RIGHT, 2, *[getattr(p.sources[0], k) for k in
+                                                               ("e0", "tau", "t0", "omega", "phase")])])
+
+
+def time_oracle(p, target_s=12.0, cells=65_536):
+    import oracle
+    probe = oracle.run(cpu_sample(p, cells, 20))
+    rate = cells * 20 / probe["seconds"]
+    steps = max(20, int(target_s * rate / cells))
+    r = oracle.run(cpu_sample(p, cells, steps))
+    return dict(value=cells * steps / r["seconds"] / 1e9, cores=r["threads"], seconds=r["seconds"],
+                sample=f"{cells} medium cells x {steps} steps of the workload (jitter slab, one source)")
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2005_05412_gb300 as mbs
+    from paper_2005_05412_gb300 import build as mbs_build
+    if rank == 0 or not os.path.exists(mbs.LIB_PATH):
+        mbs_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.set_device(local)
+    dev_index = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    p = workload(args.workload)
+    cell_steps = p.n_cells * p.n_steps
+    dev = mbs.device_from_problem(p)
+    sc = mbs.scenario_from_problem(dev, p)
+    T = args.tile
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def solve():
+        mbs.mbs_solve([sc], args.precision, "tiled", tile_steps=T, stream=stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev_index) as clk:
+        w0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            stream.wait_stream(torch.cuda.current_stream())
+            ev[k][0].record(stream)
+            solve()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+    if world > 1:
+        torch.distributed.barrier()
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_local = dev_ms / 1e3
+    if world > 1:
+        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    ctr = mbs.mbs_scenario_counters(sc)
+    launches = ctr["kernel_launches"]
+    value = cell_steps * args.steps * world / t_max / 1e9
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    # roofline of the dominant kernel (the tiled step): algorithmic bytes per
+    # cell-step = (2 + K) state values read + written, plus the 2 read-only
+    # per-cell parameters of the jittered medium
+    K = 3
+    rb = 4 if args.precision == "fp32" else 8
+    alg_bytes = (2 * (2 + K) + 2) * rb
+    tiled_launches = math.ceil(p.n_steps / T)
+    per_launch_s = t_local / args.steps / max(1, launches)
+    units_per_launch = p.n_cells * T
+    achieved = alg_bytes * units_per_launch / per_launch_s / 1e9
+    traffic = load_traffic(args)
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm or HBM_FALLBACK, "unit": "GB/s",
+            "frac": round(achieved / (hbm or HBM_FALLBACK), 4), "traffic": traffic,
+            "peak_source": "measured" if hbm else "fallback",
+            "kernel": f"k_tiled<{args.precision},N=2,percell> T={T}",
+            "alg_bytes_per_cell_step": alg_bytes, "launch_ms": round(per_launch_s * 1e3, 5),
+            "launches_per_solve": launches, "tiled_launches_per_solve": tiled_launches}
+    out = {"metric": METRIC, "value": round(value, 3), "unit": METRIC, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(t_max * 1e3 / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+           "data": "synthetic (seeded)",
+           "config": {"workload": f"{p.name}: {p.n_cells} cells x {p.n_steps} steps, N=2, per-cell jitter",
+                      "precision": args.precision, "algo": "tiled", "tile_steps": T,
+                      "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)"},
+           "roofline": roof, "clocks": clk.summary(), "gpu_launches": launches * args.steps,
+           "wall_s": round(wall, 3)}
+    if rank == 0 and not args.quick:
+        out["fp64_plain"] = fp64_plain(p, mbs, stream, torch)
+        out["e2e"] = e2e(p, mbs, args, torch, stream)
+        if world == 1 and not args.no_cpu:
+            cb = time_oracle(p)
+            out["cpu_baseline"] = {"value": round(cb["value"], 5), "unit": METRIC, "cores": cb["cores"],
+                                   "kind": "oracle", "sample": cb["sample"]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def fp64_plain(p, mbs, stream, torch, steps=4000):
+    """The plain FP64 form (one thread per cell, two launches per step) on
+    the first `steps` steps of the same workload."""
+    q = p.replace(n_steps=steps)
+    dev = mbs.device_from_problem(q)
+    sc = mbs.scenario_from_problem(dev, q)
+    res = {}
+    for algo in ("plain", "tiled"):
+        mbs.mbs_solve([sc], "fp64", algo, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mbs.mbs_solve([sc], "fp64", algo, stream=stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        res[algo] = round(q.n_cells * steps / (a.elapsed_time(b) / 1e3) / 1e9, 3)
+    return {"value": res["plain"], "fp64_tiled": res["tiled"], "unit": METRIC,
+            "sample": f"first {steps} steps of the workload"}
+
+
+def e2e(p, mbs, args, torch, stream, reps=2):
+    """End to end through the public API with host buffers: device and
+    scenario creation (host FP64 setup + host->device copies), the solve, and
+    the device->host read of every probe trace, per step."""
+    times, h2d, d2h = [], 0, 0
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dev = mbs.device_from_problem(p)
+        sc = mbs.scenario_from_problem(dev, p)
+        mbs.mbs_solve([sc], args.precision, "tiled", tile_steps=args.tile, stream=stream.cuda_stream)
+        recs = [mbs.mbs_fetch_records(sc, k) for k in range(len(p.probes))]
+        times.append(time.perf_counter() - t0)
+        c = mbs.mbs_scenario_counters(sc)
+        h2d, d2h = c["h2d_bytes"], c["d2h_bytes"]
+        assert all(np.all(np.isfinite(r)) for r in recs)
+        sc.close()
+        dev.close()
+    t = min(times)
+    return {"value": round(p.n_cells * p.n_steps / t / 1e9, 3), "unit": METRIC,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "seconds_per_step": round(t, 3)}
+
+
+def load_traffic(args):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, when it was taken on the current kernel (else null)."""
+    f = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(f))
+        key = f"{args.precision}_T{args.tile}"
+        return d.get(key)
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    p = workload(args.workload)
+    import oracle
+    oracle.build()
+    vals = []
+    for k in range(args.warmup + args.steps):
+        r = time_oracle(p, target_s=6.0, cells=32_768)
+        if k >= args.warmup:
+            vals.append(r)
+    value = float(np.mean([v["value"] for v in vals]))
+    secs = sum(v["seconds"] for v in vals)
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": METRIC, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs * 1e3 / args.steps, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded)",
+           "config": {"workload": f"{p.name}: {p.n_cells} cells x {p.n_steps} steps, N=2, per-cell jitter",
+                      "precision": "fp64", "algo": "oracle (CPU, OpenMP over cells)"},
+           "cpu_baseline": {"value": round(value, 5), "unit": METRIC, "cores": vals[0]["cores"], "kind": "oracle",
+                            "sample": vals[0]["sample"]},
+           "e2e": {"value": round(value, 5), "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sit_2lvl_jitter")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--quick", action="store_true", help="skip the FP64, e2e and CPU legs")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    run_ours(args, rank, world, local)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

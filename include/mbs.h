@@ -1,0 +1,225 @@
+/*
+ * mbs.h -- C ABI of the GB300 Maxwell-Bloch hot path.
+ *
+ * The library advances the generalized 1D Maxwell-Bloch equations of
+ * Riesch & Jirauschek, "mbsolve" (CPC 2021), Sec. 2.1 (Eqs. efield, hfield,
+ * master1D and the polarisation term) with the FDTD/operator-splitting
+ * scheme of Sec. 2.2 and Algorithm 1 (Sec. 3.2), on one CUDA GPU (sm_103a).
+ *
+ * Object model (Sec. 3.1): a *device* holds the static setup -- quantum
+ * descriptions, materials, regions, cell count, boundary reflectivities --
+ * and a *scenario* holds the dynamic part -- Courant number, end time,
+ * sources, probes -- plus the device-memory state of one simulation.
+ * mbs_solve runs Algorithm 1 for one or more scenarios; mbs_fetch_records
+ * copies probe traces to the caller.
+ *
+ * Conventions (all units SI):
+ *   - complex arrays are interleaved (re, im) doubles, matrices row-major;
+ *   - the grid has n_cells cells of width dz = length / n_cells; cell m is
+ *     centred at (m + 1/2) dz and carries E and rho; H lives on the faces
+ *     f = 0..n_cells (face f is the left face of cell f); a cell takes the
+ *     material of the first region with x_start <= centre < x_end;
+ *   - dt = courant * dz / c_max (c_max the largest light speed among the
+ *     cells' materials); n_steps = ceil(t_end / dt) unless given explicitly;
+ *   - time step n advances H to n+1/2, rho to n+1/2 (using E^n) and E to n+1;
+ *     the density matrix at n = -1/2 is rho_init, E^0 = H^{-1/2} = 0;
+ *   - record index n holds E^{n+1} / H^{n+1/2} / rho^{n+1/2}.
+ *
+ * Ownership: every create call copies its inputs; the caller may free them
+ * on return.  Objects are owned by the library until destroyed.  Device
+ * memory is allocated by the library (cudaMalloc) on the device current at
+ * mbs_scenario time.
+ *
+ * Errors: every call returns an mbs_status.  On a negative status nothing
+ * was created (out pointers are set to NULL) and mbs_last_error() returns a
+ * message for the calling thread.  No status is ever reported through a GPU
+ * fault: device-side checks set flags that mbs_solve turns into statuses.
+ */
+#ifndef MBS_H
+#define MBS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MBS_ABI_VERSION 1
+
+typedef enum {
+    MBS_OK = 0,
+    MBS_W_NOT_PSD = 1,     /* warning: the pure-dephasing rates need a
+                              non-positive-semidefinite coefficient matrix
+                              (Sec. 3.1.1); the object was still created */
+    MBS_E_INVALID = -1,    /* invalid argument (see mbs_last_error) */
+    MBS_E_CUDA = -2,       /* a CUDA runtime call failed */
+    MBS_E_OOM = -3,        /* host or device allocation failed */
+    MBS_E_NUMERIC = -4,    /* non-finite state or a density matrix that is
+                              not positive semidefinite (beyond tolerance) */
+    MBS_E_TIMEOUT = -5,    /* a bounded device-side wait gave up */
+    MBS_E_STATE = -6       /* call out of order (e.g. fetch before solve) */
+} mbs_status;
+
+typedef struct mbs_device_s *mbs_device_t;
+typedef struct mbs_scenario_s *mbs_scenario_t;
+
+/* One quantum-mechanical description (Sec. 3.1.1, class qm_description).
+ * Relaxation is the Lindblad dissipator of Eq. (lindbladdiss), given as
+ * explicit operators with rates, D(rho) = sum_k g_k (L_k rho L_k^+ -
+ * 1/2 {L_k^+ L_k, rho}), and/or in the paper's rate form: the scattering
+ * matrix R of Eq. (relax_pop) (R[i*N+j] = gamma_ij, the rate from level j
+ * into level i; diagonal ignored) plus the N(N-1)/2 pure-dephasing rates in
+ * the order 12, 13, 23, 14, 24, 34, ... .  The rate form is converted to
+ * Lindblad operators; if the dephasing rates need a non-PSD coefficient
+ * matrix, mbs_device_create returns MBS_W_NOT_PSD and keeps the (then not
+ * completely positive) dissipator. */
+typedef struct {
+    int n_levels;                 /* N >= 2 (tiled FP32 kernels: N = 2, 3) */
+    double density;               /* n3D [m^-3], >= 0 */
+    const double *h0;             /* N*N complex, Hermitian [J] */
+    const double *mu;             /* N*N complex, Hermitian dipole operator [C m] */
+    int n_lindblad;               /* >= 0 */
+    const double *lindblad_rates; /* [n_lindblad], >= 0 [1/s] */
+    const double *lindblad_ops;   /* [n_lindblad][N*N] complex */
+    const double *scattering;     /* N*N real or NULL */
+    const double *pure_dephasing; /* N(N-1)/2 real or NULL */
+    const double *rho_init;       /* N*N complex, Hermitian, trace 1, PSD */
+} mbs_qm_desc;
+
+/* Electromagnetic material (Sec. 3.1.1): relative permittivity and
+ * permeability, conductivity sigma [S/m], overlap factor Gamma, and the
+ * quantum description index (-1: no quantum systems). */
+typedef struct { double eps_r, mu_r, sigma, overlap; int qm; } mbs_material;
+
+/* Region [x_start, x_end) [m] made of material `material` (Sec. 3.1.1). */
+typedef struct { int material; double x_start, x_end; } mbs_region;
+
+/* Reflectivity of the left and right domain ends (Sec. 2.1): 0 = absorbing
+ * (first-order Mur), 1 = perfect mirror (E = 0).  Other values are rejected
+ * with MBS_E_INVALID. */
+typedef struct { double refl_left, refl_right; } mbs_bc;
+
+/* Create a device.  per_cell_jitter (optional, NULL = none) holds
+ * [n_cells][2] factors (density factor, H0 factor) multiplying n3D and H0
+ * of each cell's quantum description.  Validation: Hermitian h0, mu and
+ * rho_init (tolerance 1e-12 relative), |tr rho_init - 1| <= 1e-12, rho_init
+ * PSD, non-negative rates and density, every cell covered by a region,
+ * indices in range, eps_r, mu_r > 0.  Returns MBS_OK, MBS_W_NOT_PSD or an
+ * error. */
+int mbs_device_create(const mbs_qm_desc *qms, int n_qm,
+                      const mbs_material *mats, int n_mat,
+                      const mbs_region *regions, int n_regions,
+                      double length, int n_cells, mbs_bc bc,
+                      const double *per_cell_jitter,
+                      mbs_device_t *out);
+
+enum { MBS_SRC_TFSF_RIGHT = 0, /* one-way injection of a +x travelling wave:
+                                  total field for m >= cell (needs cell >= 2) */
+       MBS_SRC_TFSF_LEFT = 1,  /* one-way -x wave: total field for m <= cell
+                                  (needs cell <= n_cells - 3) */
+       MBS_SRC_HARD = 2 };     /* E^{n+1} at `cell` is set to the waveform */
+
+/* Source (Sec. 3.1.2, classes source / sech_pulse): waveform
+ * S(t) = e0 sech((t - t0)/tau) sin(omega t + phase) [V/m].  Soft sources
+ * are total-field/scattered-field injections that add the incident wave
+ * and stay transparent to returning waves. */
+typedef struct {
+    int kind; int cell;
+    double e0, tau, t0, omega, phase;
+} mbs_source;
+
+enum { MBS_Q_E = 0,       /* E at the cell centre, E^{n+1} [V/m] */
+       MBS_Q_H = 1,       /* H at the left face of the cell, H^{n+1/2} [A/m] */
+       MBS_Q_RHO_RE = 2,  /* Re rho_ij^{n+1/2} of the cell */
+       MBS_Q_RHO_IM = 3 };/* Im rho_ij^{n+1/2} */
+
+/* Probe (Sec. 3.1.2, class record): one quantity at one cell, recorded
+ * every step.  i, j are 0-based level indices for MBS_Q_RHO_*. */
+typedef struct { int cell; int quantity; int i, j; } mbs_probe;
+
+/* Create a scenario on `dev`: builds the propagators for dt in FP64 on the
+ * host, allocates the device state on the current CUDA device and uploads
+ * it.  dt = dt_or_0 if > 0, else courant * dz / c_max (courant in (0, 1]);
+ * dt must not exceed dz / c_max.  n_steps > 0 overrides t_end. */
+int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end, long long n_steps,
+                 const mbs_source *src, int n_src,
+                 const mbs_probe *probes, int n_probes,
+                 mbs_scenario_t *out);
+
+enum { MBS_PREC_FP64 = 0,      /* FP64 state and arithmetic */
+       MBS_PREC_FP32 = 1 };    /* FP32 fields and Bloch deviations with
+                                  compensated (Kahan) accumulation */
+enum { MBS_ALGO_AUTO = 0,
+       MBS_ALGO_PLAIN = 1,     /* one thread per cell, two launches per step
+                                  (Algorithm 1 as written) */
+       MBS_ALGO_TILED = 2 };   /* temporal tiles: tile_steps steps per launch
+                                  with halo recompute (the redundant-calculation
+                                  loop of Sec. 3.2) */
+
+typedef struct {
+    int precision;     /* MBS_PREC_* */
+    int algo;          /* MBS_ALGO_* */
+    int tile_steps;    /* steps per tiled launch (multiple of 4), 0 = default */
+    int check_every;   /* steps between device-side state checks, 0 = only at the end */
+} mbs_opts;
+
+/* Run every scenario from its initial condition to its last step (previous
+ * results are discarded).  `cuda_stream` is a cudaStream_t or NULL for the
+ * legacy default stream.  The call returns after the work has completed.
+ * Returns MBS_E_NUMERIC if a state check found a non-finite value or a
+ * density-matrix eigenvalue below -1e-6. */
+int mbs_solve(mbs_scenario_t *batch, int n_scen, const mbs_opts *opts, void *cuda_stream);
+
+/* Copy probe `probe`'s trace (n_steps doubles, SI units) into out.  With
+ * out == NULL only *n_written is set (the required count).  Returns
+ * MBS_E_INVALID if cap is too small, MBS_E_STATE before the first solve. */
+int mbs_fetch_records(mbs_scenario_t s, int probe, double *out, size_t cap, size_t *n_written);
+
+/* Grid facts of a scenario: dt [s], dz [m], number of steps. */
+int mbs_scenario_info(mbs_scenario_t s, double *dt, double *dz, long long *n_steps);
+
+/* State diagnostics of the last solve over the probe cells and a strided
+ * sample of medium cells (FP64 on the device): max |tr rho - 1|, smallest
+ * eigenvalue of rho, number of steps run. */
+int mbs_scenario_stats(mbs_scenario_t s, double *max_trace_dev, double *min_eig, long long *n_steps);
+
+/* Host-side introspection of the FP64 setup (no GPU needed): for quantum
+ * description `qm` of `dev` at time step dt, the real generator in the
+ * dipole eigenbasis and the derived step operators.  With N levels,
+ * K = N*N - 1 and P = N(N-1)/2, each non-NULL output receives:
+ *   lambda[N]     eigenvalues of mu (ascending) [C m]
+ *   V[N*N]        complex eigenvectors of mu (columns), interleaved
+ *   A[K*K]        linear part of one full step exp(L0 dt) on Bloch
+ *                 deviations (row-major)
+ *   Ah[N*N*N*N]   exp(L0 dt/2) on the full real coordinates
+ *   c[K]          affine offset of exp(L0 dt) at the reference state
+ *   zref[N*N]     reference state (full real coordinates)
+ *   g[K], g0      d_t P / n3D = g . u + g0 for the rotated deviation u
+ * The real coordinates of rho are, in the eigenbasis of mu (rho~ = V^+ rho
+ * V): rho~_kk for k < N, then Re rho~_jk, Im rho~_jk for the pairs j < k in
+ * the order (0,1), (0,2), ..., (0,N-1), (1,2), ... ; the Bloch deviation
+ * coordinates drop rho~_{N-1,N-1}. */
+int mbs_device_propagators(mbs_device_t dev, int qm, double dt,
+                           double *lambda, double *V, double *A, double *Ah,
+                           double *c, double *zref, double *g, double *g0);
+
+/* Transfer and launch counters: bytes copied host -> device by the
+ * scenario's creation and its solves so far, bytes copied device -> host by
+ * the last solve and the fetches after it, CUDA kernel launches issued by
+ * the last solve. */
+int mbs_scenario_counters(mbs_scenario_t s, long long *h2d_bytes, long long *d2h_bytes,
+                          long long *kernel_launches);
+
+void mbs_scenario_destroy(mbs_scenario_t s);
+void mbs_device_destroy(mbs_device_t d);
+
+/* Message for the last non-OK status on the calling thread ("" if none). */
+const char *mbs_last_error(void);
+
+/* Library version, equals MBS_ABI_VERSION. */
+int mbs_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MBS_H */

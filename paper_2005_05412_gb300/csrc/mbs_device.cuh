@@ -1,0 +1,703 @@
+#pragma once
+// mbs_device.cuh -- sm_103a device code of the 1D Maxwell-Bloch time step
+// (included by the kernel translation units).
+//
+// Two forms of the same per-step arithmetic (see mbs_internal.h for the
+// state representation):
+//
+//  * plain (Algorithm 1 as written, Sec. 3.2): one thread per cell, two
+//    launches per step -- {H, rho, d_t P} then {E, sources, boundaries,
+//    records} -- with the kernel boundary as the paper's sync();
+//
+//  * tiled (the redundant-calculation loop of Sec. 3.2, re-designed for the
+//    GPU): each warp owns a segment of cells and advances it T steps per
+//    launch entirely in registers.  A lane holds R consecutive cells; the
+//    only neighbour traffic is one warp shuffle of E to the right and one of
+//    H to the left per step.  The warp loads its segment plus a T-cell halo
+//    on each side; the halo shrinks by one cell per side per step (the
+//    light cone of the 3-point stencil), so after T steps the owned cells
+//    are exact and are the only ones written back.  Ping-pong buffers keep
+//    neighbouring warps' halo reads race-free.  No shared-memory traffic or
+//    block barrier happens inside the time loop.
+//
+// The field rotation needs sin(theta) and cos(theta) - 1 of small angles to
+// full relative precision; they come from their Taylor series (coefficients
+// +-1/n!) for |theta| <= 1/2 and from the CUDA math library otherwise.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mbs_internal.h"
+
+namespace mbs {
+namespace dev {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ------------------------------------------------------------- math helpers
+__device__ __forceinline__ void sincos_m1(float x, float &s, float &cm1) {
+  if (fabsf(x) <= 0.5f) {
+    const float t = x * x;
+    float ps = fmaf(t, 1.0f / 362880.0f, -1.0f / 5040.0f);
+    ps = fmaf(t, ps, 1.0f / 120.0f);
+    ps = fmaf(t, ps, -1.0f / 6.0f);
+    ps = fmaf(t, ps, 1.0f);
+    s = x * ps;
+    float pc = fmaf(t, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+    pc = fmaf(t, pc, -1.0f / 720.0f);
+    pc = fmaf(t, pc, 1.0f / 24.0f);
+    pc = fmaf(t, pc, -0.5f);
+    cm1 = t * pc;
+  } else {
+    float c;
+    sincosf(x, &s, &c);
+    cm1 = c - 1.0f;
+  }
+}
+
+__device__ __forceinline__ void sincos_m1(double x, double &s, double &cm1) {
+  if (fabs(x) <= 0.5) {
+    const double t = x * x;
+    // sin x / x and (cos x - 1) / x^2 to order x^16
+    double ps = 1.0 / 355687428096000.0;          // 1/17!
+    ps = fma(t, ps, -1.0 / 1307674368000.0);      // 1/15!
+    ps = fma(t, ps, 1.0 / 6227020800.0);          // 1/13!
+    ps = fma(t, ps, -1.0 / 39916800.0);           // 1/11!
+    ps = fma(t, ps, 1.0 / 362880.0);              // 1/9!
+    ps = fma(t, ps, -1.0 / 5040.0);
+    ps = fma(t, ps, 1.0 / 120.0);
+    ps = fma(t, ps, -1.0 / 6.0);
+    ps = fma(t, ps, 1.0);
+    s = x * ps;
+    double pc = -1.0 / 6402373705728000.0;        // 1/18!
+    pc = fma(t, pc, 1.0 / 20922789888000.0);      // 1/16!
+    pc = fma(t, pc, -1.0 / 87178291200.0);        // 1/14!
+    pc = fma(t, pc, 1.0 / 479001600.0);           // 1/12!
+    pc = fma(t, pc, -1.0 / 3628800.0);            // 1/10!
+    pc = fma(t, pc, 1.0 / 40320.0);
+    pc = fma(t, pc, -1.0 / 720.0);
+    pc = fma(t, pc, 1.0 / 24.0);
+    pc = fma(t, pc, -0.5);
+    cm1 = t * pc;
+  } else {
+    double c;
+    sincos(x, &s, &c);
+    cm1 = c - 1.0;
+  }
+}
+
+// compensated d += x (Kahan): c carries the part of past additions that
+// rounding dropped (true value = d - c)
+template <typename real>
+__device__ __forceinline__ void kahan_add(real &d, real &c, real x) {
+  const real y = x - c;
+  const real t = d + y;
+  c = (t - d) - y;
+  d = t;
+}
+
+// ---------------------------------------------------- parameter accessors
+// contiguous parameter block: am1 | c | w | w0 | kap | zr
+template <typename real, int N>
+struct PrmBlock {
+  static constexpr int K = N * N - 1, P = N * (N - 1) / 2;
+  const real *p;
+  __device__ __forceinline__ real am1(int i, int j) const { return p[i * K + j]; }
+  __device__ __forceinline__ real c(int i) const { return p[K * K + i]; }
+  __device__ __forceinline__ real w(int i) const { return p[K * K + K + i]; }
+  __device__ __forceinline__ real w0() const { return p[K * K + 2 * K]; }
+  __device__ __forceinline__ real kap(int q) const { return p[K * K + 2 * K + 1 + q]; }
+  __device__ __forceinline__ real zr(int i) const { return p[K * K + 2 * K + 1 + P + i]; }
+};
+
+// per-cell rows (am1, c, w, w0 strided by ld) + material block for kap, zr
+template <typename real, int N>
+struct PrmCell {
+  static constexpr int K = N * N - 1, P = N * (N - 1) / 2;
+  const real *p;   // &pcell[0][cell]
+  int ld;
+  const real *mb;  // material block
+  __device__ __forceinline__ real am1(int i, int j) const { return p[(size_t)(i * K + j) * ld]; }
+  __device__ __forceinline__ real c(int i) const { return p[(size_t)(K * K + i) * ld]; }
+  __device__ __forceinline__ real w(int i) const { return p[(size_t)(K * K + K + i) * ld]; }
+  __device__ __forceinline__ real w0() const { return p[(size_t)(K * K + 2 * K) * ld]; }
+  __device__ __forceinline__ real kap(int q) const { return mb[K * K + 2 * K + 1 + q]; }
+  __device__ __forceinline__ real zr(int i) const { return mb[K * K + 2 * K + 1 + P + i]; }
+};
+
+// per-cell parameters held in registers (tiled kernel, N = 2)
+template <typename real, int N>
+struct PrmReg {
+  static constexpr int K = N * N - 1, P = N * (N - 1) / 2;
+  real a[K * K], cc[K], ww[K], ww0;
+  const real *mb;
+  __device__ __forceinline__ real am1(int i, int j) const { return a[i * K + j]; }
+  __device__ __forceinline__ real c(int i) const { return cc[i]; }
+  __device__ __forceinline__ real w(int i) const { return ww[i]; }
+  __device__ __forceinline__ real w0() const { return ww0; }
+  __device__ __forceinline__ real kap(int q) const { return mb[K * K + 2 * K + 1 + q]; }
+  __device__ __forceinline__ real zr(int i) const { return mb[K * K + 2 * K + 1 + P + i]; }
+};
+
+// ------------------------------------------------- one cell's Bloch step
+// delta^n -> delta^{n+1}; returns the coupling w . u + w0 and leaves the
+// rotated deviation u (= v - x_ref) in `u`.
+template <typename real, int N, bool KAHAN, class Prm>
+__device__ __forceinline__ real bloch_step(const Prm &q, real e, real (&d)[N * N - 1],
+                                           real (&cc)[N * N - 1], real (&u)[N * N - 1]) {
+  constexpr int K = N * N - 1, P = N * (N - 1) / 2, NP = N - 1;
+  real rx[2 * P];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) u[i] = d[i];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    real s, cm1;
+    sincos_m1(q.kap(p) * e, s, cm1);
+    const int ia = NP + 2 * p, ib = ia + 1;
+    const real xa = q.zr(2 * p) + d[ia];
+    const real xb = q.zr(2 * p + 1) + d[ib];
+    const real ra = cm1 * xa - s * xb;
+    const real rb = s * xa + cm1 * xb;
+    rx[2 * p] = ra;
+    rx[2 * p + 1] = rb;
+    u[ia] = d[ia] + ra;
+    u[ib] = d[ib] + rb;
+  }
+  real pw = q.w0();
+#pragma unroll
+  for (int i = 0; i < K; ++i) pw += q.w(i) * u[i];
+  if constexpr (K <= 15) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      real acc = q.c(i);
+      if (i >= NP) acc += rx[i - NP];
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc += q.am1(i, j) * u[j];
+      if (KAHAN)
+        kahan_add(d[i], cc[i], acc);
+      else
+        d[i] += acc;
+    }
+  } else {
+    // large K: rows stay rolled (keeps code size and compile time bounded)
+#pragma unroll 1
+    for (int i = 0; i < K; ++i) {
+      real acc = q.c(i);
+      if (i >= NP) acc += rx[i - NP];
+#pragma unroll 5
+      for (int j = 0; j < K; ++j) acc += q.am1(i, j) * u[j];
+      if (KAHAN)
+        kahan_add(d[i], cc[i], acc);
+      else
+        d[i] += acc;
+    }
+  }
+  return pw;
+}
+
+template <typename real, int N>
+__device__ __forceinline__ real probe_rho(const real *coef, const real (&u)[N * N - 1]) {
+  constexpr int K = N * N - 1;
+  real v = coef[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) v += coef[i] * u[i];
+  return v;
+}
+
+template <typename real>
+__device__ __forceinline__ real emc_at(const Args &a, int idx, int k) {
+  return reinterpret_cast<const real *>(a.emc)[a.mat[idx] * 4 + k];
+}
+
+// ========================================================= plain path
+// Launch A of step n: H on faces 1..nx-1 (in place), rho and d_t P per cell.
+template <typename real, int N, bool KAHAN>
+__global__ void k_plain_a(const Args a, long long n, int cur) {
+  constexpr int K = N * N - 1;
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= a.nx) return;
+  const int idx = a.off + m;
+  const real *E = reinterpret_cast<const real *>(a.E[cur]);
+  real *H = reinterpret_cast<real *>(a.H[0]);
+  if (m >= 1) {
+    real h = H[idx] + emc_at<real>(a, idx, 2) * (E[idx] - E[idx - 1]);
+    for (int s = 0; s < a.n_src; ++s)
+      if (a.src[s].face == m) h += reinterpret_cast<const real *>(a.src[s].sH)[n];
+    H[idx] = h;
+  }
+  real *pd = reinterpret_cast<real *>(a.pd);
+  const int slot = a.qslot[a.mat[idx]];
+  if (slot < 0) {
+    pd[idx] = real(0);
+    return;
+  }
+  real *D = reinterpret_cast<real *>(a.D[0]);
+  real *Cc = reinterpret_cast<real *>(a.C[0]);
+  real d[K], cc[K], u[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    d[i] = D[(size_t)i * a.ld + idx];
+    cc[i] = KAHAN ? Cc[(size_t)i * a.ld + idx] : real(0);
+  }
+  const real *mb = reinterpret_cast<const real *>(a.qpar) + (size_t)slot * a.qstride;
+  real pw;
+  if (a.pcell) {
+    PrmCell<real, N> q{reinterpret_cast<const real *>(a.pcell) + idx, a.ld, mb};
+    pw = bloch_step<real, N, KAHAN>(q, E[idx], d, cc, u);
+  } else {
+    PrmBlock<real, N> q{mb};
+    pw = bloch_step<real, N, KAHAN>(q, E[idx], d, cc, u);
+  }
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    D[(size_t)i * a.ld + idx] = d[i];
+    if (KAHAN) Cc[(size_t)i * a.ld + idx] = cc[i];
+  }
+  pd[idx] = pw;
+  for (int p = 0; p < a.n_probe; ++p)
+    if (a.pr_cell[p] == m && a.pr_q[p] >= 2)
+      reinterpret_cast<real *>(a.rec)[(size_t)p * a.nt + n] =
+          probe_rho<real, N>(reinterpret_cast<const real *>(a.pr_coef) + (size_t)p * (K + 1), u);
+}
+
+template <typename real>
+__device__ __forceinline__ real e_update(const Args &a, const real *E, const real *H, const real *pd,
+                                         int m, long long n, bool *hard) {
+  const int idx = a.off + m;
+  real e = emc_at<real>(a, idx, 0) * E[idx] - pd[idx] + emc_at<real>(a, idx, 1) * (H[idx + 1] - H[idx]);
+  for (int s = 0; s < a.n_src; ++s)
+    if (a.src[s].cell == m) {
+      const real v = reinterpret_cast<const real *>(a.src[s].sE)[n];
+      if (a.src[s].kind == 2) {
+        e = v;
+        *hard = true;
+      } else {
+        e += v;
+      }
+    }
+  return e;
+}
+
+// Launch B of step n: E^{n+1} into E[cur ^ 1], sources, boundaries, records.
+template <typename real>
+__global__ void k_plain_b(const Args a, long long n, int cur) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= a.nx) return;
+  const int idx = a.off + m;
+  const real *E = reinterpret_cast<const real *>(a.E[cur]);
+  real *En = reinterpret_cast<real *>(a.E[cur ^ 1]);
+  const real *H = reinterpret_cast<const real *>(a.H[0]);
+  const real *pd = reinterpret_cast<const real *>(a.pd);
+  bool hard = false;
+  real e = e_update<real>(a, E, H, pd, m, n, &hard);
+  if (m == 0 && a.nx > 1) {
+    if (a.bc_l == 1) {
+      e = real(0);
+    } else {
+      bool h2 = false;
+      const real e1 = e_update<real>(a, E, H, pd, 1, n, &h2);
+      e = E[idx + 1] + real(a.kmur_l) * (e1 - E[idx]);
+    }
+  } else if (m == a.nx - 1 && a.nx > 1) {
+    if (a.bc_r == 1) {
+      e = real(0);
+    } else {
+      bool h2 = false;
+      const real e1 = e_update<real>(a, E, H, pd, m - 1, n, &h2);
+      e = E[idx - 1] + real(a.kmur_r) * (e1 - E[idx]);
+    }
+  }
+  En[idx] = e;
+  for (int p = 0; p < a.n_probe; ++p)
+    if (a.pr_cell[p] == m && a.pr_q[p] < 2)
+      reinterpret_cast<real *>(a.rec)[(size_t)p * a.nt + n] = a.pr_q[p] == 0 ? e : H[idx];
+}
+
+// ========================================================= tiled path
+template <typename real, int R>
+__device__ __forceinline__ void ld_row(const real *p, real (&v)[R]) {
+#pragma unroll
+  for (int j = 0; j < R; ++j) v[j] = p[j];
+}
+template <>
+__device__ __forceinline__ void ld_row<float, 4>(const float *p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4 *>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+template <>
+__device__ __forceinline__ void ld_row<double, 2>(const double *p, double (&v)[2]) {
+  const double2 t = *reinterpret_cast<const double2 *>(p);
+  v[0] = t.x; v[1] = t.y;
+}
+template <>
+__device__ __forceinline__ void ld_row<double, 4>(const double *p, double (&v)[4]) {
+  const double2 t = reinterpret_cast<const double2 *>(p)[0];
+  const double2 u = reinterpret_cast<const double2 *>(p)[1];
+  v[0] = t.x; v[1] = t.y; v[2] = u.x; v[3] = u.y;
+}
+template <typename real, int R>
+__device__ __forceinline__ void st_row(real *p, const real (&v)[R]) {
+#pragma unroll
+  for (int j = 0; j < R; ++j) p[j] = v[j];
+}
+template <>
+__device__ __forceinline__ void st_row<float, 4>(float *p, const float (&v)[4]) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void st_row<double, 2>(double *p, const double (&v)[2]) {
+  *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+}
+template <>
+__device__ __forceinline__ void st_row<double, 4>(double *p, const double (&v)[4]) {
+  reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// Warp w owns cells [w*own, (w+1)*own), own = 32 R - 2 T; lane l holds cells
+// tb + l R .. tb + l R + R - 1 with tb = w*own - T.  Reads buffers `cur`,
+// writes the owned cells of buffers cur ^ 1.  PERCELL: per-cell propagator
+// rows are loaded into registers (jittered media).
+template <typename real, int N, int R, bool KAHAN, bool PERCELL>
+__global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int nsteps, int T, int cur) {
+  constexpr int K = N * N - 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real *s_emc = reinterpret_cast<real *>(smem_raw);
+  real *s_q = s_emc + a.n_mat_all * 4;
+  int *s_slot = reinterpret_cast<int *>(s_q + a.n_slot * a.qstride);
+  for (int i = threadIdx.x; i < a.n_mat_all * 4; i += blockDim.x) s_emc[i] = reinterpret_cast<const real *>(a.emc)[i];
+  for (int i = threadIdx.x; i < a.n_slot * a.qstride; i += blockDim.x) s_q[i] = reinterpret_cast<const real *>(a.qpar)[i];
+  for (int i = threadIdx.x; i < a.n_mat_all; i += blockDim.x) s_slot[i] = a.qslot[i];
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int own = 32 * R - 2 * T;
+  const int c_own = warp * own;
+  if (c_own >= a.nx) return;   // whole warp leaves together
+  const int tb = c_own - T;
+  const int g0 = tb + lane * R;         // first cell of this lane
+  const int base = a.off + g0;          // its array index (>= 0, multiple of R)
+
+  const real *Ein = reinterpret_cast<const real *>(a.E[cur]);
+  const real *Hin = reinterpret_cast<const real *>(a.H[cur]);
+  const real *Din = reinterpret_cast<const real *>(a.D[cur]);
+  const real *Cin = reinterpret_cast<const real *>(a.C[cur]);
+
+  real E[R], H[R], ca[R], cb[R], ch[R];
+  real d[K][R], cc[K][R];
+  ld_row<real, R>(Ein + base, E);
+  ld_row<real, R>(Hin + base, H);
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    ld_row<real, R>(Din + (size_t)i * a.ld + base, d[i]);
+    if (KAHAN) ld_row<real, R>(Cin + (size_t)i * a.ld + base, cc[i]);
+    else
+#pragma unroll
+      for (int j = 0; j < R; ++j) cc[i][j] = real(0);
+  }
+  unsigned med = 0;
+  int slot = -1;
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int mt = a.mat[base + j];
+    ca[j] = s_emc[mt * 4 + 0];
+    cb[j] = s_emc[mt * 4 + 1];
+    ch[j] = (g0 + j == 0) ? real(0) : s_emc[mt * 4 + 2];   // face 0 is a fixed boundary slot
+    const int sl = s_slot[mt];
+    if (sl >= 0) {
+      med |= 1u << j;
+      slot = sl;
+    }
+  }
+  const real *mb = s_q + (slot < 0 ? 0 : slot) * a.qstride;
+
+  PrmReg<real, N> pr[PERCELL ? R : 1];
+  if (PERCELL) {
+    const real *pc = reinterpret_cast<const real *>(a.pcell);
+#pragma unroll
+    for (int j = 0; j < (PERCELL ? R : 1); ++j) {
+      pr[j].mb = mb;
+#pragma unroll
+      for (int i = 0; i < K * K; ++i) pr[j].a[i] = pc[(size_t)i * a.ld + base + j];
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        pr[j].cc[i] = pc[(size_t)(K * K + i) * a.ld + base + j];
+        pr[j].ww[i] = pc[(size_t)(K * K + K + i) * a.ld + base + j];
+      }
+      pr[j].ww0 = pc[(size_t)(K * K + 2 * K) * a.ld + base + j];
+    }
+  }
+
+  // warp-uniform: does the tile touch a source, a boundary cell, a probe?
+  const int t_lo = tb, t_hi = tb + 32 * R;   // [t_lo, t_hi)
+  bool any_src = false;
+  for (int s = 0; s < a.n_src; ++s)
+    any_src |= (a.src[s].cell >= t_lo && a.src[s].cell < t_hi) || (a.src[s].face >= t_lo && a.src[s].face < t_hi);
+  const bool any_bnd = (t_lo <= 0 && 0 < t_hi) || (t_lo <= a.nx - 1 && a.nx - 1 < t_hi);
+  // probes owned by this lane
+  unsigned pmask = 0;
+  const int ti0 = lane * R;
+  for (int p = 0; p < a.n_probe; ++p) {
+    const int j = a.pr_cell[p] - g0;
+    if (j >= 0 && j < R && ti0 + j >= T && ti0 + j < 32 * R - T) pmask |= 1u << j;
+  }
+  const bool any_probe = __any_sync(FULL, pmask != 0);
+  real *rec = reinterpret_cast<real *>(a.rec);
+  const real *pcoef = reinterpret_cast<const real *>(a.pr_coef);
+
+#pragma unroll 1
+  for (int t = 0; t < nsteps; ++t) {
+    const long long n = n0 + t;
+    // ---- H^{n+1/2} on the left faces of my cells
+    const real el = __shfl_up_sync(FULL, E[R - 1], 1);
+    real Hn[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) Hn[j] = H[j] + ch[j] * (E[j] - (j ? E[j - 1] : el));
+    if (any_src) {
+      for (int s = 0; s < a.n_src; ++s) {
+        const int f = a.src[s].face - g0;
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+          if (f == j) Hn[j] += reinterpret_cast<const real *>(a.src[s].sH)[n];
+      }
+    }
+    // ---- rho^{n+1/2} and the coupling term
+    real pw[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      pw[j] = real(0);
+      if (med & (1u << j)) {
+        real dj[K], cj[K], u[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          dj[i] = d[i][j];
+          cj[i] = cc[i][j];
+        }
+        if (PERCELL)
+          pw[j] = bloch_step<real, N, KAHAN>(pr[PERCELL ? j : 0], E[j], dj, cj, u);
+        else
+          pw[j] = bloch_step<real, N, KAHAN>(PrmBlock<real, N>{mb}, E[j], dj, cj, u);
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          d[i][j] = dj[i];
+          cc[i][j] = cj[i];
+        }
+        if (pmask & (1u << j)) {
+          for (int p = 0; p < a.n_probe; ++p)
+            if (a.pr_cell[p] == g0 + j && a.pr_q[p] >= 2)
+              rec[(size_t)p * a.nt + n] = probe_rho<real, N>(pcoef + (size_t)p * (K + 1), u);
+        }
+      }
+    }
+    // ---- E^{n+1}
+    const real hr = __shfl_down_sync(FULL, Hn[0], 1);
+    real En[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) En[j] = ca[j] * E[j] - pw[j] + cb[j] * ((j < R - 1 ? Hn[j + 1] : hr) - Hn[j]);
+    if (any_src) {
+      for (int s = 0; s < a.n_src; ++s) {
+        const int c = a.src[s].cell - g0;
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+          if (c == j) {
+            const real v = reinterpret_cast<const real *>(a.src[s].sE)[n];
+            En[j] = a.src[s].kind == 2 ? v : En[j] + v;
+          }
+      }
+    }
+    if (any_bnd) {
+      const real ero = __shfl_down_sync(FULL, E[0], 1);
+      const real ern = __shfl_down_sync(FULL, En[0], 1);
+      const real elo = __shfl_up_sync(FULL, E[R - 1], 1);
+      const real eln = __shfl_up_sync(FULL, En[R - 1], 1);
+      real Eb[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) Eb[j] = En[j];
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        if (g0 + j == 0) {
+          const real e1o = j < R - 1 ? E[j + 1] : ero;
+          const real e1n = j < R - 1 ? En[j + 1] : ern;
+          Eb[j] = a.bc_l == 1 ? real(0) : e1o + real(a.kmur_l) * (e1n - E[j]);
+        }
+        if (g0 + j == a.nx - 1) {
+          const real e1o = j ? E[j - 1] : elo;
+          const real e1n = j ? En[j - 1] : eln;
+          Eb[j] = a.bc_r == 1 ? real(0) : e1o + real(a.kmur_r) * (e1n - E[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < R; ++j) En[j] = Eb[j];
+    }
+    if (any_probe && pmask) {
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        if (pmask & (1u << j))
+          for (int p = 0; p < a.n_probe; ++p)
+            if (a.pr_cell[p] == g0 + j && a.pr_q[p] < 2)
+              rec[(size_t)p * a.nt + n] = a.pr_q[p] == 0 ? En[j] : Hn[j];
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      E[j] = En[j];
+      H[j] = Hn[j];
+    }
+  }
+
+  // ---- write back the owned cells (never past the last cell)
+  const bool owned = ti0 >= T && ti0 < 32 * R - T;   // T is a multiple of R
+  if (!owned) return;
+  real *Eo = reinterpret_cast<real *>(a.E[cur ^ 1]);
+  real *Ho = reinterpret_cast<real *>(a.H[cur ^ 1]);
+  real *Do = reinterpret_cast<real *>(a.D[cur ^ 1]);
+  real *Co = reinterpret_cast<real *>(a.C[cur ^ 1]);
+  if (g0 + R <= a.nx) {
+    st_row<real, R>(Eo + base, E);
+    st_row<real, R>(Ho + base, H);
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      st_row<real, R>(Do + (size_t)i * a.ld + base, d[i]);
+      if (KAHAN) st_row<real, R>(Co + (size_t)i * a.ld + base, cc[i]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      if (g0 + j < a.nx) {
+        Eo[base + j] = E[j];
+        Ho[base + j] = H[j];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          Do[(size_t)i * a.ld + base + j] = d[i][j];
+          if (KAHAN) Co[(size_t)i * a.ld + base + j] = cc[i][j];
+        }
+      }
+  }
+}
+
+// ========================================================= state check
+// For each listed cell, rebuild the stored density matrix x (FP64, true
+// value delta - compensation, reference state zref[slot][N*N] in full real
+// coordinates), and report its trace deviation and smallest eigenvalue
+// (cyclic Jacobi on the Hermitian N x N matrix).  Non-finite values set
+// bit 0 of flags[0].
+template <typename real, int N>
+__global__ void k_check(const Args a, int cur, const int *cells, int n_cells, double *min_eig,
+                        double *tr_dev, const double *zref) {
+  constexpr int K = N * N - 1, NP = N - 1;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_cells) return;
+  const int m = cells[k];
+  const int idx = a.off + m;
+  const int slot = a.qslot[a.mat[idx]];
+  if (slot < 0) {
+    min_eig[k] = 1.0;
+    tr_dev[k] = 0.0;
+    return;
+  }
+  zref += (size_t)slot * N * N;
+  const real *D = reinterpret_cast<const real *>(a.D[cur]);
+  const real *Cc = reinterpret_cast<const real *>(a.C[cur]);
+  double y[N * N];
+  double popsum = 0.0;
+  bool finite = true;
+  for (int i = 0; i < K; ++i) {
+    double v = (double)D[(size_t)i * a.ld + idx];
+    if (a.prec == 1) v -= (double)Cc[(size_t)i * a.ld + idx];
+    finite &= isfinite(v);
+    const int fi = i < NP ? i : i + 1;
+    y[fi] = zref[fi] + v;
+    if (i < NP) popsum += v;
+  }
+  y[NP] = zref[NP] - popsum;
+  double re[N][N], im[N][N];
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) re[i][j] = im[i][j] = 0.0;
+  double tr = 0.0;
+  for (int i = 0; i < N; ++i) {
+    re[i][i] = y[i];
+    tr += y[i];
+  }
+  int q = 0;
+  for (int i = 0; i < N; ++i)
+    for (int j = i + 1; j < N; ++j, ++q) {
+      re[i][j] = re[j][i] = y[N + 2 * q];
+      im[i][j] = y[N + 2 * q + 1];
+      im[j][i] = -y[N + 2 * q + 1];
+    }
+  // cyclic complex Jacobi: rotate away |a_pq| with the phase-removed real rotation
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j)
+        if (i != j) off += re[i][j] * re[i][j] + im[i][j] * im[i][j];
+    if (off < 1e-30) break;
+    for (int p = 0; p < N - 1; ++p)
+      for (int r = p + 1; r < N; ++r) {
+        const double mag = hypot(re[p][r], im[p][r]);
+        if (mag < 1e-300) continue;
+        const double pr = re[p][r] / mag, pi = im[p][r] / mag;   // e^{i phi}
+        const double tau = (re[r][r] - re[p][p]) / (2.0 * mag);
+        const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + tt * tt), s = tt * c;
+        // W: identity except W_pp = c, W_pr = s, W_rp = -s e^{-i phi}, W_rr = c e^{-i phi}
+        // A <- W^+ A W  (columns then rows)
+        for (int i = 0; i < N; ++i) {   // A W : columns p, r
+          const double ap_r = re[i][p], ap_i = im[i][p], ar_r = re[i][r], ar_i = im[i][r];
+          // col p: c a_p - s e^{-i phi} a_r
+          const double er = pr * ar_r + pi * ar_i, ei = pr * ar_i - pi * ar_r;   // e^{-i phi} a_r
+          re[i][p] = c * ap_r - s * er;
+          im[i][p] = c * ap_i - s * ei;
+          re[i][r] = s * ap_r + c * er;
+          im[i][r] = s * ap_i + c * ei;
+        }
+        for (int j = 0; j < N; ++j) {   // W^+ A : rows p, r
+          const double ap_r = re[p][j], ap_i = im[p][j], ar_r = re[r][j], ar_i = im[r][j];
+          const double er = pr * ar_r - pi * ar_i, ei = pr * ar_i + pi * ar_r;   // e^{+i phi} a_r
+          re[p][j] = c * ap_r - s * er;
+          im[p][j] = c * ap_i - s * ei;
+          re[r][j] = s * ap_r + c * er;
+          im[r][j] = s * ap_i + c * ei;
+        }
+        re[p][r] = re[r][p] = im[p][r] = im[r][p] = 0.0;
+      }
+  }
+  double mn = re[0][0];
+  for (int i = 1; i < N; ++i) mn = fmin(mn, re[i][i]);
+  if (!finite || !isfinite(mn)) {
+    atomicOr(a.flags, 1);
+    mn = -1e300;
+  }
+  min_eig[k] = mn;
+  tr_dev[k] = fabs(tr - 1.0);
+}
+
+template <typename real, int N, bool KAHAN>
+int plain_step_impl(const Args &a, long long n, int cur, cudaStream_t st) {
+  const int bs = 256, gs = (a.nx + bs - 1) / bs;
+  k_plain_a<real, N, KAHAN><<<gs, bs, 0, st>>>(a, n, cur);
+  k_plain_b<real><<<gs, bs, 0, st>>>(a, n, cur);
+  return (int)cudaGetLastError();
+}
+
+template <typename real, int N, int R, bool KAHAN, bool PERCELL>
+int tiled_impl(const Args &a, long long n0, int nsteps, int T, int cur, cudaStream_t st) {
+  const int own = 32 * R - 2 * T;
+  const int n_warps = (a.nx + own - 1) / own;
+  const int bs = 128, wpb = bs / 32;
+  const int gs = (n_warps + wpb - 1) / wpb;
+  const size_t sm = sizeof(real) * (a.n_mat_all * 4 + a.n_slot * a.qstride) + sizeof(int) * a.n_mat_all + 16;
+  k_tiled<real, N, R, KAHAN, PERCELL><<<gs, bs, sm, st>>>(a, n0, nsteps, T, cur);
+  return (int)cudaGetLastError();
+}
+
+template <typename real, int N>
+int check_impl(const Args &a, int cur, const int *cells, int n_cells, double *mn, double *tr, const double *z,
+               cudaStream_t st) {
+  const int bs = 128, gs = (n_cells + bs - 1) / bs;
+  k_check<real, N><<<gs, bs, 0, st>>>(a, cur, cells, n_cells, mn, tr, z);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace dev
+}  // namespace mbs

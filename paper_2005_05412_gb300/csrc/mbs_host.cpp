@@ -1,0 +1,1245 @@
+// mbs_host.cpp -- host side of the GB300 Maxwell-Bloch hot path: C-ABI
+// entry points (include/mbs.h), input validation, the FP64 setup of the
+// per-material step operators, device buffers and the solve loop.
+//
+// FP64 setup per quantum description (Sec. 2.2 operator splitting, Sec. 3.1
+// Lindblad relaxation):
+//   * mu = V diag(lambda) V^+ by Householder reduction of the Hermitian
+//     matrix to real symmetric tridiagonal form followed by implicit QL
+//     iterations (Golub & Van Loan, Secs. 8.3 and 8.5);
+//   * the Liouvillian L0 (H0 and the dissipator of Eq. lindbladdiss) as a
+//     real matrix on the coordinates of rho~ = V^+ rho V (mbs_internal.h);
+//     the rate form (Eq. relax_pop, pure dephasing) becomes Lindblad
+//     operators |i><j| and diag(v_k), the latter from the double-centred
+//     dephasing matrix G = -1/2 J D J (D_ij = 2 gamma_ij,p), which is PSD iff
+//     the dephasing rates admit a PSD coefficient matrix;
+//   * exp(L0 dt) and exp(L0 dt/2) by Taylor series with scaling and
+//     squaring;
+//   * the steady state of L0 (when unique) as the deviation reference.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "../../include/mbs.h"
+#include "mbs_internal.h"
+
+using cd = std::complex<double>;
+
+namespace {
+
+constexpr double kPlanck = 6.62607015e-34;  // CODATA 2018
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kHbar = kPlanck / (2.0 * kPi);
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kMu0 = 1.25663706212e-6;
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? MBS_E_OOM : MBS_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------ linear algebra
+void cmatmul(int n, const cd *a, const cd *b, cd *c) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      cd s = 0;
+      for (int k = 0; k < n; ++k) s += a[i * n + k] * b[k * n + j];
+      c[i * n + j] = s;
+    }
+}
+
+void rmatmul(int n, const double *a, const double *b, double *c) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0;
+      for (int k = 0; k < n; ++k) s += a[i * n + k] * b[k * n + j];
+      c[i * n + j] = s;
+    }
+}
+
+// X^+ A X for n x n complex matrices
+std::vector<cd> conj_transform(int n, const std::vector<cd> &X, const cd *A) {
+  std::vector<cd> t(n * n), xh(n * n), out(n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) xh[i * n + j] = std::conj(X[j * n + i]);
+  cmatmul(n, xh.data(), A, t.data());
+  cmatmul(n, t.data(), X.data(), out.data());
+  return out;
+}
+
+// Hermitian eigen-decomposition (ascending eigenvalues, eigenvectors in the
+// columns of V): Householder reduction to Hermitian tridiagonal form, a
+// diagonal phase change to real symmetric tridiagonal, implicit QL with
+// Wilkinson-type shifts on (d, e).
+bool eigh_hq(int n, const cd *A, double *w, cd *V) {
+  std::vector<cd> a(A, A + n * n), Q(n * n, 0.0);
+  for (int i = 0; i < n; ++i) Q[i * n + i] = 1.0;
+  std::vector<cd> v(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    double xn = 0;
+    for (int i = k + 1; i < n; ++i) xn += std::norm(a[i * n + k]);
+    xn = std::sqrt(xn);
+    if (xn == 0) continue;
+    const cd x0 = a[(k + 1) * n + k];
+    const cd ph = std::abs(x0) > 0 ? x0 / std::abs(x0) : cd(1.0);
+    const cd alpha = -ph * xn;
+    std::fill(v.begin(), v.end(), cd(0));
+    for (int i = k + 1; i < n; ++i) v[i] = a[i * n + k];
+    v[k + 1] -= alpha;
+    double vn = 0;
+    for (int i = k + 1; i < n; ++i) vn += std::norm(v[i]);
+    if (vn == 0) continue;
+    const double f = 2.0 / vn;
+    for (int j = 0; j < n; ++j) {  // a <- (I - f v v^+) a
+      cd s = 0;
+      for (int i = k + 1; i < n; ++i) s += std::conj(v[i]) * a[i * n + j];
+      for (int i = k + 1; i < n; ++i) a[i * n + j] -= f * v[i] * s;
+    }
+    for (int i = 0; i < n; ++i) {  // a <- a (I - f v v^+), Q <- Q (I - f v v^+)
+      cd s = 0, sq = 0;
+      for (int j = k + 1; j < n; ++j) {
+        s += a[i * n + j] * v[j];
+        sq += Q[i * n + j] * v[j];
+      }
+      for (int j = k + 1; j < n; ++j) {
+        a[i * n + j] -= f * s * std::conj(v[j]);
+        Q[i * n + j] -= f * sq * std::conj(v[j]);
+      }
+    }
+  }
+  // phases making the sub-diagonal real and non-negative
+  std::vector<double> d(n), e(n, 0.0);
+  std::vector<cd> ph(n, 1.0);
+  for (int k = 0; k < n; ++k) d[k] = a[k * n + k].real();
+  for (int k = 0; k + 1 < n; ++k) {
+    const cd b = a[(k + 1) * n + k];
+    const double r = std::abs(b);
+    e[k] = r;
+    ph[k + 1] = r > 0 ? ph[k] * (b / r) : ph[k];
+  }
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) Q[i * n + k] *= ph[k];
+  // implicit QL on the symmetric tridiagonal (d, e); Z accumulates rotations
+  std::vector<double> z(n * n, 0.0);
+  for (int i = 0; i < n; ++i) z[i * n + i] = 1.0;
+  for (int l = 0; l < n; ++l) {
+    int iter = 0;
+    for (;;) {
+      int m = l;
+      for (; m + 1 < n; ++m) {
+        const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+        if (std::fabs(e[m]) <= DBL_EPSILON * dd) break;
+      }
+      if (m == l) break;
+      if (++iter > 100) return false;
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = std::hypot(g, 1.0);
+      g = d[m] - d[l] + e[l] / (g + std::copysign(r, g));
+      double s = 1.0, c = 1.0, p = 0.0;
+      int i = m - 1;
+      bool early = false;
+      for (; i >= l; --i) {
+        double f = s * e[i];
+        const double b = c * e[i];
+        r = std::hypot(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {
+          d[i + 1] -= p;
+          e[m] = 0.0;
+          early = true;
+          break;
+        }
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - p;
+        r = (d[i] - g) * s + 2.0 * c * b;
+        p = s * r;
+        d[i + 1] = g + p;
+        g = c * r - b;
+        for (int k = 0; k < n; ++k) {
+          f = z[k * n + i + 1];
+          z[k * n + i + 1] = s * z[k * n + i] + c * f;
+          z[k * n + i] = c * z[k * n + i] - s * f;
+        }
+      }
+      if (early) continue;
+      d[l] -= p;
+      e[l] = g;
+      e[m] = 0.0;
+    }
+  }
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int x, int y) { return d[x] < d[y]; });
+  for (int k = 0; k < n; ++k) {
+    w[k] = d[ord[k]];
+    for (int i = 0; i < n; ++i) {
+      cd s = 0;
+      for (int j = 0; j < n; ++j) s += Q[i * n + j] * z[j * n + ord[k]];
+      V[i * n + k] = s;
+    }
+  }
+  return true;
+}
+
+// exp(A) for a real n x n matrix: scale by 2^-s until ||A||_1 <= 1/4, sum
+// the Taylor series to order 20 (remainder < 1e-32 relative), square s times.
+void expm_taylor(int n, const double *A, double *X) {
+  double nrm = 0;
+  for (int j = 0; j < n; ++j) {
+    double s = 0;
+    for (int i = 0; i < n; ++i) s += std::fabs(A[i * n + j]);
+    nrm = std::max(nrm, s);
+  }
+  if (!std::isfinite(nrm)) {
+    for (int i = 0; i < n * n; ++i) X[i] = std::nan("");
+    return;
+  }
+  int sq = 0;
+  while (nrm > 0.25) {
+    nrm *= 0.5;
+    ++sq;
+  }
+  const double sc = std::ldexp(1.0, -sq);
+  std::vector<double> B(n * n), term(n * n, 0.0), t2(n * n);
+  for (int i = 0; i < n * n; ++i) B[i] = A[i] * sc;
+  for (int i = 0; i < n * n; ++i) X[i] = 0;
+  for (int i = 0; i < n; ++i) X[i * n + i] = term[i * n + i] = 1.0;
+  for (int k = 1; k <= 20; ++k) {
+    rmatmul(n, term.data(), B.data(), t2.data());
+    for (int i = 0; i < n * n; ++i) {
+      term[i] = t2[i] / k;
+      X[i] += term[i];
+    }
+  }
+  for (int k = 0; k < sq; ++k) {
+    rmatmul(n, X, X, t2.data());
+    std::copy(t2.begin(), t2.end(), X);
+  }
+}
+
+// Solve A x = b (n x n, partial pivoting).  Returns the smallest |pivot|
+// relative to max |A|, or -1 on exact singularity.
+double solve(int n, std::vector<double> A, std::vector<double> &b) {
+  double amax = 0;
+  for (double x : A) amax = std::max(amax, std::fabs(x));
+  double pmin = 1e300;
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A[i * n + k]) > std::fabs(A[p * n + k])) p = i;
+    if (A[p * n + k] == 0) return -1;
+    pmin = std::min(pmin, std::fabs(A[p * n + k]));
+    if (p != k) {
+      for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[p * n + j]);
+      std::swap(b[k], b[p]);
+    }
+    for (int i = k + 1; i < n; ++i) {
+      const double f = A[i * n + k] / A[k * n + k];
+      for (int j = k; j < n; ++j) A[i * n + j] -= f * A[k * n + j];
+      b[i] -= f * b[k];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    double s = b[k];
+    for (int j = k + 1; j < n; ++j) s -= A[k * n + j] * b[j];
+    b[k] = s / A[k * n + k];
+  }
+  return amax > 0 ? pmin / amax : 0;
+}
+
+// ------------------------------------------------- real coordinates of rho~
+// y[k] = rho~_kk (k < N); pair q = (j, k), j < k: y[N+2q] = Re, y[N+2q+1] = Im
+void herm_to_y(int N, const cd *X, double *y) {
+  for (int k = 0; k < N; ++k) y[k] = X[k * N + k].real();
+  int q = 0;
+  for (int j = 0; j < N; ++j)
+    for (int k = j + 1; k < N; ++k, ++q) {
+      y[N + 2 * q] = X[j * N + k].real();
+      y[N + 2 * q + 1] = X[j * N + k].imag();
+    }
+}
+
+void y_to_herm(int N, const double *y, cd *X) {
+  for (int i = 0; i < N * N; ++i) X[i] = 0;
+  for (int k = 0; k < N; ++k) X[k * N + k] = y[k];
+  int q = 0;
+  for (int j = 0; j < N; ++j)
+    for (int k = j + 1; k < N; ++k, ++q) {
+      X[j * N + k] = cd(y[N + 2 * q], y[N + 2 * q + 1]);
+      X[k * N + j] = cd(y[N + 2 * q], -y[N + 2 * q + 1]);
+    }
+}
+
+// full index of Bloch-deviation index i (drops rho~_{N-1,N-1})
+inline int full_of(int N, int i) { return i < N - 1 ? i : i + 1; }
+
+struct QDesc {
+  int N = 0;
+  double n3d = 0;
+  std::vector<double> lambda;   // eigenvalues of mu
+  std::vector<cd> V;            // eigenvectors (columns)
+  std::vector<double> MH, MD;   // generator parts on full coords (N^2 x N^2)
+  std::vector<double> yref, yinit;
+  bool unique_steady = false;
+};
+
+struct Step {  // FP64 step operators for one (description, H0 factor)
+  std::vector<double> AK, c, g, Ah;
+  double g0 = 0;
+};
+
+void build_step(const QDesc &q, double hfac, double dt, Step &s) {
+  const int N = q.N, N2 = N * N, K = N2 - 1;
+  std::vector<double> M(N2 * N2), Mh(N2 * N2), A(N2 * N2);
+  for (int i = 0; i < N2 * N2; ++i) M[i] = hfac * q.MH[i] + q.MD[i];
+  for (int i = 0; i < N2 * N2; ++i) Mh[i] = 0.5 * dt * M[i];
+  s.Ah.assign(N2 * N2, 0.0);
+  expm_taylor(N2, Mh.data(), s.Ah.data());
+  rmatmul(N2, s.Ah.data(), s.Ah.data(), A.data());
+  s.AK.assign(K * K, 0.0);
+  for (int i = 0; i < K; ++i)
+    for (int j = 0; j < K; ++j) {
+      const int fi = full_of(N, i), fj = full_of(N, j);
+      s.AK[i * K + j] = A[fi * N2 + fj] - (j < N - 1 ? A[fi * N2 + N - 1] : 0.0);
+    }
+  std::vector<double> ay(N2, 0.0);
+  for (int i = 0; i < N2; ++i)
+    for (int j = 0; j < N2; ++j) ay[i] += A[i * N2 + j] * q.yref[j];
+  s.c.assign(K, 0.0);
+  for (int i = 0; i < K; ++i) s.c[i] = ay[full_of(N, i)] - q.yref[full_of(N, i)];
+  // d_t P / n3D = tr(mu L0 exp(L0 dt/2) v) = sum_j lambda_j [M Ah y]_j
+  std::vector<double> MAh(N2 * N2);
+  rmatmul(N2, M.data(), s.Ah.data(), MAh.data());
+  std::vector<double> gf(N2, 0.0);
+  for (int j = 0; j < N; ++j)
+    for (int c = 0; c < N2; ++c) gf[c] += q.lambda[j] * MAh[j * N2 + c];
+  s.g.assign(K, 0.0);
+  for (int i = 0; i < K; ++i) s.g[i] = gf[full_of(N, i)] - (i < N - 1 ? gf[N - 1] : 0.0);
+  s.g0 = 0;
+  for (int c = 0; c < N2; ++c) s.g0 += gf[c] * q.yref[c];
+}
+
+// Lab-basis functional rho_ab = h . y (real part if im == 0, imaginary part
+// otherwise) on the full coordinates.
+std::vector<double> rho_functional(const QDesc &q, int a, int b, bool im) {
+  const int N = q.N;
+  std::vector<double> h(N * N, 0.0);
+  auto put = [&](int idx, cd v) { h[idx] = im ? v.imag() : v.real(); };
+  for (int j = 0; j < N; ++j) put(j, q.V[a * N + j] * std::conj(q.V[b * N + j]));
+  int p = 0;
+  for (int j = 0; j < N; ++j)
+    for (int k = j + 1; k < N; ++k, ++p) {
+      const cd x = q.V[a * N + j] * std::conj(q.V[b * N + k]);
+      const cd y = q.V[a * N + k] * std::conj(q.V[b * N + j]);
+      put(N + 2 * p, x + y);
+      put(N + 2 * p + 1, cd(0, 1) * (x - y));
+    }
+  return h;
+}
+
+}  // namespace
+
+// ============================================================ objects
+struct MatDesc {
+  double eps_r, mu_r, sigma, overlap;
+  int qm;
+};
+
+struct mbs_device_s {
+  std::vector<QDesc> qms;
+  std::vector<MatDesc> mats;
+  int nx = 0;
+  double length = 0, dz = 0;
+  int bc_l = 0, bc_r = 0;
+  std::vector<uint8_t> cell_mat;   // [nx]
+  std::vector<double> jitter;      // [nx][2] or empty
+  int N = 0;                       // common level count of the media (0: none)
+};
+
+struct SrcHost {
+  int kind, face, cell;
+  std::vector<double> sH, sE;
+};
+
+struct Bundle {  // device buffers of one precision
+  bool ready = false;
+  size_t rb = 8;
+  void *E[2] = {}, *H[2] = {}, *D[2] = {}, *C[2] = {}, *pd = nullptr, *Dinit = nullptr;
+  void *emc = nullptr, *qpar = nullptr, *pcell = nullptr, *pr_coef = nullptr, *rec = nullptr;
+  std::vector<void *> src_tabs;
+};
+
+struct mbs_scenario_s {
+  mbs_device_s *dev = nullptr;
+  double dt = 0;
+  long long nt = 0;
+  int N = 0, K = 0, P = 0;
+  int ld = 0, off = mbs::PAD;
+  int n_slot = 0, qstride = 0;
+  // FP64 master copies
+  std::vector<double> emc, qpar, pcell, Dinit, pr_coef, zref;
+  std::vector<int> qslot, pr_cell, pr_q;
+  std::vector<SrcHost> src;
+  double kmur_l = 0, kmur_r = 0;
+  bool has_pcell = false;
+  // device
+  uint8_t *d_mat = nullptr;
+  int *d_qslot = nullptr, *d_pr_cell = nullptr, *d_pr_q = nullptr, *d_flags = nullptr, *d_chk_cells = nullptr;
+  double *d_zref = nullptr, *d_chk_min = nullptr, *d_chk_tr = nullptr;
+  std::vector<int> chk_cells;
+  Bundle b[2];
+  int solved_prec = -1, last_cur = 0;
+  long long h2d_bytes = 0, d2h_bytes = 0, launches = 0;
+  long long steps_run = 0;
+  double st_trace = 0, st_min = 0;
+  int device_id = 0;
+};
+
+namespace {
+
+bool herm_ok(int n, const double *m, double tol_rel) {
+  double mx = 0;
+  for (int i = 0; i < 2 * n * n; ++i) mx = std::max(mx, std::fabs(m[i]));
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double dr = m[2 * (i * n + j)] - m[2 * (j * n + i)];
+      const double di = m[2 * (i * n + j) + 1] + m[2 * (j * n + i) + 1];
+      if (std::fabs(dr) > tol_rel * mx || std::fabs(di) > tol_rel * mx) return false;
+    }
+  return true;
+}
+
+std::vector<cd> load(int n, const double *m) {
+  std::vector<cd> v(n * n);
+  for (int i = 0; i < n * n; ++i) v[i] = cd(m[2 * i], m[2 * i + 1]);
+  return v;
+}
+
+// Build one quantum description; returns MBS_OK / MBS_W_NOT_PSD / error.
+int build_qdesc(const mbs_qm_desc &in, QDesc &q) {
+  const int N = in.n_levels;
+  if (N < 2 || N > mbs::NMAX) return fail(MBS_E_INVALID, "n_levels %d outside [2, %d]", N, mbs::NMAX);
+  if (!in.h0 || !in.mu || !in.rho_init) return fail(MBS_E_INVALID, "h0, mu and rho_init are required");
+  if (!(in.density >= 0)) return fail(MBS_E_INVALID, "negative density");
+  if (!herm_ok(N, in.h0, 1e-12)) return fail(MBS_E_INVALID, "h0 is not Hermitian");
+  if (!herm_ok(N, in.mu, 1e-12)) return fail(MBS_E_INVALID, "mu is not Hermitian");
+  if (!herm_ok(N, in.rho_init, 1e-12)) return fail(MBS_E_INVALID, "rho_init is not Hermitian");
+  if (in.n_lindblad < 0 || (in.n_lindblad > 0 && (!in.lindblad_rates || !in.lindblad_ops)))
+    return fail(MBS_E_INVALID, "Lindblad operators missing");
+  for (int k = 0; k < in.n_lindblad; ++k)
+    if (!(in.lindblad_rates[k] >= 0)) return fail(MBS_E_INVALID, "negative Lindblad rate");
+  if (in.scattering)
+    for (int i = 0; i < N * N; ++i)
+      if (i % (N + 1) != 0 && !(in.scattering[i] >= 0)) return fail(MBS_E_INVALID, "negative scattering rate");
+  if (in.pure_dephasing)
+    for (int i = 0; i < N * (N - 1) / 2; ++i)
+      if (!(in.pure_dephasing[i] >= 0)) return fail(MBS_E_INVALID, "negative pure dephasing rate");
+  q.N = N;
+  q.n3d = in.density;
+  std::vector<cd> h0 = load(N, in.h0), mu = load(N, in.mu), rho0 = load(N, in.rho_init);
+  cd tr = 0;
+  for (int i = 0; i < N; ++i) tr += rho0[i * N + i];
+  if (std::abs(tr - 1.0) > 1e-12) return fail(MBS_E_INVALID, "trace of rho_init is not 1");
+  {
+    std::vector<double> w(N);
+    std::vector<cd> vv(N * N);
+    if (!eigh_hq(N, rho0.data(), w.data(), vv.data())) return fail(MBS_E_INVALID, "eig(rho_init) failed");
+    if (w[0] < -1e-12) return fail(MBS_E_INVALID, "rho_init is not positive semidefinite");
+  }
+  q.lambda.assign(N, 0.0);
+  q.V.assign(N * N, 0.0);
+  if (!eigh_hq(N, mu.data(), q.lambda.data(), q.V.data())) return fail(MBS_E_INVALID, "eig(mu) failed");
+
+  // Lindblad operators in the lab basis
+  std::vector<std::vector<cd>> ops;
+  std::vector<double> rates;
+  for (int k = 0; k < in.n_lindblad; ++k) {
+    ops.push_back(load(N, in.lindblad_ops + (size_t)2 * N * N * k));
+    rates.push_back(in.lindblad_rates[k]);
+  }
+  int status = MBS_OK;
+  if (in.scattering)
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j)
+        if (i != j && in.scattering[i * N + j] > 0) {
+          std::vector<cd> op(N * N, 0.0);
+          op[i * N + j] = 1.0;
+          ops.push_back(op);
+          rates.push_back(in.scattering[i * N + j]);
+        }
+  if (in.pure_dephasing) {
+    // G = -1/2 J D J with D_ij = 2 gamma_ij,p: then 1/2 (G_ii + G_jj - 2 G_ij)
+    // = gamma_ij,p, and diag ops v_k with rates g_k (G = sum g_k v_k v_k^T)
+    // give exactly -gamma_ij,p on rho_ij.
+    std::vector<double> D(N * N, 0.0), G(N * N, 0.0);
+    int p = 0;
+    for (int j = 1; j < N; ++j)
+      for (int i = 0; i < j; ++i, ++p) D[i * N + j] = D[j * N + i] = 2.0 * in.pure_dephasing[p];
+    std::vector<double> rm(N, 0.0);
+    double all = 0;
+    for (int i = 0; i < N; ++i) {
+      for (int j = 0; j < N; ++j) rm[i] += D[i * N + j] / N;
+      all += rm[i] / N;
+    }
+    double gmax = 0;
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        G[i * N + j] = -0.5 * (D[i * N + j] - rm[i] - rm[j] + all);
+        gmax = std::max(gmax, std::fabs(G[i * N + j]));
+      }
+    std::vector<cd> Gc(G.begin(), G.end()), Gv(N * N);
+    std::vector<double> gw(N);
+    if (!eigh_hq(N, Gc.data(), gw.data(), Gv.data())) return fail(MBS_E_INVALID, "eig(G) failed");
+    for (int k = 0; k < N; ++k) {
+      if (gw[k] < -1e-12 * gmax) status = MBS_W_NOT_PSD;
+      if (std::fabs(gw[k]) <= 1e-14 * gmax) continue;
+      std::vector<cd> op(N * N, 0.0);
+      for (int i = 0; i < N; ++i) op[i * N + i] = Gv[i * N + k].real();
+      ops.push_back(op);
+      rates.push_back(gw[k]);
+    }
+  }
+
+  // generators in the dipole eigenbasis, column by column
+  const int N2 = N * N;
+  std::vector<cd> Ht = conj_transform(N, q.V, h0.data());
+  std::vector<std::vector<cd>> Lt, LL;
+  for (auto &op : ops) {
+    Lt.push_back(conj_transform(N, q.V, op.data()));
+    std::vector<cd> lh(N2), ll(N2);
+    const auto &L = Lt.back();
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) lh[i * N + j] = std::conj(L[j * N + i]);
+    cmatmul(N, lh.data(), L.data(), ll.data());
+    LL.push_back(ll);
+  }
+  q.MH.assign(N2 * N2, 0.0);
+  q.MD.assign(N2 * N2, 0.0);
+  std::vector<double> e(N2), col(N2);
+  std::vector<cd> X(N2), T1(N2), T2(N2), R(N2), lh(N2);
+  for (int c = 0; c < N2; ++c) {
+    std::fill(e.begin(), e.end(), 0.0);
+    e[c] = 1.0;
+    y_to_herm(N, e.data(), X.data());
+    cmatmul(N, Ht.data(), X.data(), T1.data());
+    cmatmul(N, X.data(), Ht.data(), T2.data());
+    for (int i = 0; i < N2; ++i) R[i] = cd(0, -1.0 / kHbar) * (T1[i] - T2[i]);
+    herm_to_y(N, R.data(), col.data());
+    for (int i = 0; i < N2; ++i) q.MH[i * N2 + c] = col[i];
+    std::fill(R.begin(), R.end(), cd(0));
+    for (size_t k = 0; k < Lt.size(); ++k) {
+      const auto &L = Lt[k];
+      for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) lh[i * N + j] = std::conj(L[j * N + i]);
+      cmatmul(N, L.data(), X.data(), T1.data());
+      cmatmul(N, T1.data(), lh.data(), T2.data());
+      for (int i = 0; i < N2; ++i) R[i] += rates[k] * T2[i];
+      cmatmul(N, LL[k].data(), X.data(), T1.data());
+      cmatmul(N, X.data(), LL[k].data(), T2.data());
+      for (int i = 0; i < N2; ++i) R[i] -= 0.5 * rates[k] * (T1[i] + T2[i]);
+    }
+    herm_to_y(N, R.data(), col.data());
+    for (int i = 0; i < N2; ++i) q.MD[i * N2 + c] = col[i];
+  }
+  // reference state: the steady state of L0 if unique, else rho_init
+  q.yinit.assign(N2, 0.0);
+  {
+    std::vector<cd> rt = conj_transform(N, q.V, rho0.data());
+    herm_to_y(N, rt.data(), q.yinit.data());
+  }
+  std::vector<double> M(N2 * N2), b(N2, 0.0);
+  for (int i = 0; i < N2 * N2; ++i) M[i] = q.MH[i] + q.MD[i];
+  for (int c = 0; c < N2; ++c) M[(N - 1) * N2 + c] = c < N ? 1.0 : 0.0;  // trace row
+  b[N - 1] = 1.0;
+  const double piv = solve(N2, M, b);
+  q.unique_steady = piv > 1e-9;
+  q.yref = q.unique_steady ? b : q.yinit;
+  return status;
+}
+
+size_t rsize(int prec) { return prec == 0 ? sizeof(double) : sizeof(float); }
+
+thread_local long long *g_h2d = nullptr;   // byte counter of the current upload phase
+
+// upload a double vector as `prec` reals
+int upload(const std::vector<double> &h, void **dptr, int prec) {
+  const size_t n = h.size();
+  if (n == 0) {
+    *dptr = nullptr;
+    return 0;
+  }
+  cudaError_t e = cudaMalloc(dptr, n * rsize(prec));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  if (g_h2d) *g_h2d += (long long)(n * rsize(prec));
+  if (prec == 0) {
+    e = cudaMemcpy(*dptr, h.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+  } else {
+    std::vector<float> f(n);
+    for (size_t i = 0; i < n; ++i) f[i] = (float)h[i];
+    e = cudaMemcpy(*dptr, f.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  return 0;
+}
+
+template <typename T>
+int upload_raw(const std::vector<T> &h, T **dptr) {
+  if (h.empty()) {
+    *dptr = nullptr;
+    return 0;
+  }
+  if (g_h2d) *g_h2d += (long long)(h.size() * sizeof(T));
+  cudaError_t e = cudaMalloc((void **)dptr, h.size() * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  e = cudaMemcpy(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  return 0;
+}
+
+void free_bundle(Bundle &b) {
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(b.E[i]);
+    cudaFree(b.H[i]);
+    cudaFree(b.D[i]);
+    cudaFree(b.C[i]);
+  }
+  cudaFree(b.pd);
+  cudaFree(b.Dinit);
+  cudaFree(b.emc);
+  cudaFree(b.qpar);
+  cudaFree(b.pcell);
+  cudaFree(b.pr_coef);
+  cudaFree(b.rec);
+  for (void *p : b.src_tabs) cudaFree(p);
+  b = Bundle();
+}
+
+int ensure_bundle(mbs_scenario_s *s, int prec) {
+  Bundle &b = s->b[prec];
+  if (b.ready) return 0;
+  const size_t rb = rsize(prec);
+  b.rb = rb;
+  const size_t row = (size_t)s->ld * rb;
+  const int K = s->K;
+  cudaError_t e;
+  for (int i = 0; i < 2; ++i) {
+    if ((e = cudaMalloc(&b.E[i], row)) != cudaSuccess) return cuda_fail(e, "cudaMalloc E");
+    if ((e = cudaMalloc(&b.H[i], row)) != cudaSuccess) return cuda_fail(e, "cudaMalloc H");
+    if ((e = cudaMalloc(&b.D[i], row * std::max(K, 1))) != cudaSuccess) return cuda_fail(e, "cudaMalloc D");
+    if ((e = cudaMalloc(&b.C[i], row * std::max(K, 1))) != cudaSuccess) return cuda_fail(e, "cudaMalloc C");
+  }
+  if ((e = cudaMalloc(&b.pd, row)) != cudaSuccess) return cuda_fail(e, "cudaMalloc pd");
+  int rc;
+  if ((rc = upload(s->Dinit, &b.Dinit, prec))) return rc;
+  if ((rc = upload(s->emc, &b.emc, prec))) return rc;
+  if ((rc = upload(s->qpar, &b.qpar, prec))) return rc;
+  if (s->has_pcell && (rc = upload(s->pcell, &b.pcell, prec))) return rc;
+  if ((rc = upload(s->pr_coef, &b.pr_coef, prec))) return rc;
+  const size_t nrec = std::max<size_t>(1, s->pr_cell.size()) * (size_t)s->nt;
+  if ((e = cudaMalloc(&b.rec, nrec * rb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc records");
+  if ((e = cudaMemset(b.rec, 0, nrec * rb)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
+  for (auto &sr : s->src) {
+    void *p = nullptr;
+    if ((rc = upload(sr.sH, &p, prec))) return rc;
+    b.src_tabs.push_back(p);
+    if ((rc = upload(sr.sE, &p, prec))) return rc;
+    b.src_tabs.push_back(p);
+  }
+  b.ready = true;
+  return 0;
+}
+
+mbs::Args make_args(mbs_scenario_s *s, int prec) {
+  Bundle &b = s->b[prec];
+  mbs::Args a{};
+  a.prec = prec;
+  a.N = s->N;
+  a.K = s->K;
+  a.P = s->P;
+  a.nx = s->dev->nx;
+  a.ld = s->ld;
+  a.off = s->off;
+  a.nt = s->nt;
+  for (int i = 0; i < 2; ++i) {
+    a.E[i] = b.E[i];
+    a.H[i] = b.H[i];
+    a.D[i] = b.D[i];
+    a.C[i] = b.C[i];
+  }
+  a.pd = b.pd;
+  a.mat = s->d_mat;
+  a.n_mat_all = (int)s->qslot.size();
+  a.emc = b.emc;
+  a.qslot = s->d_qslot;
+  a.qpar = b.qpar;
+  a.n_slot = s->n_slot;
+  a.qstride = s->qstride;
+  a.pcell = s->has_pcell ? b.pcell : nullptr;
+  a.n_src = (int)s->src.size();
+  for (size_t k = 0; k < s->src.size(); ++k) {
+    a.src[k].kind = s->src[k].kind;
+    a.src[k].face = s->src[k].face;
+    a.src[k].cell = s->src[k].cell;
+    a.src[k].sH = b.src_tabs[2 * k];
+    a.src[k].sE = b.src_tabs[2 * k + 1];
+  }
+  a.bc_l = s->dev->bc_l;
+  a.bc_r = s->dev->bc_r;
+  a.kmur_l = s->kmur_l;
+  a.kmur_r = s->kmur_r;
+  a.n_probe = (int)s->pr_cell.size();
+  a.pr_cell = s->d_pr_cell;
+  a.pr_q = s->d_pr_q;
+  a.pr_coef = b.pr_coef;
+  a.rec = b.rec;
+  a.flags = s->d_flags;
+  return a;
+}
+
+void free_scenario(mbs_scenario_s *s) {
+  for (auto &b : s->b) free_bundle(b);
+  cudaFree(s->d_mat);
+  cudaFree(s->d_qslot);
+  cudaFree(s->d_pr_cell);
+  cudaFree(s->d_pr_q);
+  cudaFree(s->d_flags);
+  cudaFree(s->d_chk_cells);
+  cudaFree(s->d_zref);
+  cudaFree(s->d_chk_min);
+  cudaFree(s->d_chk_tr);
+}
+
+double light_speed(const MatDesc &m) { return 1.0 / std::sqrt(kEps0 * m.eps_r * kMu0 * m.mu_r); }
+
+}  // namespace
+
+// ============================================================ C ABI
+extern "C" {
+
+const char *mbs_last_error(void) { return g_err.c_str(); }
+
+int mbs_abi_version(void) { return MBS_ABI_VERSION; }
+
+int mbs_device_create(const mbs_qm_desc *qms, int n_qm, const mbs_material *mats, int n_mat,
+                      const mbs_region *regions, int n_regions, double length, int n_cells, mbs_bc bc,
+                      const double *per_cell_jitter, mbs_device_t *out) {
+  g_err.clear();
+  if (!out) return fail(MBS_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n_qm < 0 || (n_qm > 0 && !qms)) return fail(MBS_E_INVALID, "bad quantum description list");
+  if (n_mat < 1 || n_mat > 250 || !mats) return fail(MBS_E_INVALID, "need 1..250 materials");
+  if (n_regions < 1 || !regions) return fail(MBS_E_INVALID, "need at least one region");
+  if (!(length > 0) || n_cells < 8) return fail(MBS_E_INVALID, "need length > 0 and n_cells >= 8");
+  if (n_cells > (1 << 30)) return fail(MBS_E_INVALID, "n_cells too large");
+  auto refl = [](double r) { return r == 0.0 ? 0 : (r == 1.0 ? 1 : -1); };
+  if (refl(bc.refl_left) < 0 || refl(bc.refl_right) < 0)
+    return fail(MBS_E_INVALID, "reflectivity must be 0 (absorbing) or 1 (mirror)");
+  auto dev = std::make_unique<mbs_device_s>();
+  dev->nx = n_cells;
+  dev->length = length;
+  dev->dz = length / n_cells;
+  dev->bc_l = refl(bc.refl_left);
+  dev->bc_r = refl(bc.refl_right);
+  int status = MBS_OK;
+  for (int i = 0; i < n_qm; ++i) {
+    QDesc q;
+    const int rc = build_qdesc(qms[i], q);
+    if (rc < 0) return rc;
+    if (rc == MBS_W_NOT_PSD) status = MBS_W_NOT_PSD;
+    dev->qms.push_back(std::move(q));
+  }
+  for (int i = 0; i < n_mat; ++i) {
+    const mbs_material &m = mats[i];
+    if (!(m.eps_r > 0) || !(m.mu_r > 0) || !(m.sigma >= 0) || !(m.overlap >= 0))
+      return fail(MBS_E_INVALID, "material %d: need eps_r, mu_r > 0, sigma, overlap >= 0", i);
+    if (m.qm < -1 || m.qm >= n_qm) return fail(MBS_E_INVALID, "material %d: bad quantum description index", i);
+    dev->mats.push_back({m.eps_r, m.mu_r, m.sigma, m.overlap, m.qm});
+  }
+  for (int r = 0; r < n_regions; ++r)
+    if (regions[r].material < 0 || regions[r].material >= n_mat)
+      return fail(MBS_E_INVALID, "region %d: bad material index", r);
+  dev->cell_mat.resize(n_cells);
+  for (int m = 0; m < n_cells; ++m) {
+    const double x = (m + 0.5) * dev->dz;
+    int k = -1;
+    for (int r = 0; r < n_regions; ++r)
+      if (x >= regions[r].x_start && x < regions[r].x_end) {
+        k = regions[r].material;
+        break;
+      }
+    if (k < 0) return fail(MBS_E_INVALID, "cell %d (x = %g m) lies in no region", m, x);
+    dev->cell_mat[m] = (uint8_t)k;
+    const int q = dev->mats[k].qm;
+    if (q >= 0) {
+      if (dev->N == 0) dev->N = dev->qms[q].N;
+      if (dev->qms[q].N != dev->N) return fail(MBS_E_INVALID, "media with different level counts in one device");
+    }
+  }
+  if (per_cell_jitter) {
+    dev->jitter.assign(per_cell_jitter, per_cell_jitter + (size_t)2 * n_cells);
+    for (double v : dev->jitter)
+      if (!std::isfinite(v) || v < 0) return fail(MBS_E_INVALID, "per-cell factors must be finite and >= 0");
+  }
+  *out = dev.release();
+  return status;
+}
+
+void mbs_device_destroy(mbs_device_t d) { delete d; }
+
+int mbs_device_propagators(mbs_device_t dev, int qm, double dt, double *lambda, double *V, double *A,
+                           double *Ah, double *c, double *zref, double *g, double *g0) {
+  g_err.clear();
+  if (!dev || qm < 0 || qm >= (int)dev->qms.size() || !(dt > 0)) return fail(MBS_E_INVALID, "bad arguments");
+  const QDesc &q = dev->qms[qm];
+  const int N = q.N, N2 = N * N, K = N2 - 1;
+  Step s;
+  build_step(q, 1.0, dt, s);
+  if (lambda) std::copy(q.lambda.begin(), q.lambda.end(), lambda);
+  if (V)
+    for (int i = 0; i < N2; ++i) {
+      V[2 * i] = q.V[i].real();
+      V[2 * i + 1] = q.V[i].imag();
+    }
+  if (A) std::copy(s.AK.begin(), s.AK.end(), A);
+  if (Ah) std::copy(s.Ah.begin(), s.Ah.end(), Ah);
+  if (c) std::copy(s.c.begin(), s.c.end(), c);
+  if (zref) std::copy(q.yref.begin(), q.yref.end(), zref);
+  if (g) std::copy(s.g.begin(), s.g.end(), g);
+  if (g0) *g0 = s.g0;
+  (void)K;
+  return MBS_OK;
+}
+
+int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end, long long n_steps,
+                 const mbs_source *src, int n_src, const mbs_probe *probes, int n_probes, mbs_scenario_t *out) {
+  g_err.clear();
+  if (!out) return fail(MBS_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!dev) return fail(MBS_E_INVALID, "device is NULL");
+  if (n_src < 0 || n_src > mbs::MAXSRC || (n_src && !src)) return fail(MBS_E_INVALID, "0..%d sources", mbs::MAXSRC);
+  if (n_probes < 0 || n_probes > mbs::MAXPROBE || (n_probes && !probes))
+    return fail(MBS_E_INVALID, "0..%d probes", mbs::MAXPROBE);
+  const int nx = dev->nx;
+  const double dz = dev->dz;
+  double cmax = 0;
+  for (int m = 0; m < nx; ++m) cmax = std::max(cmax, light_speed(dev->mats[dev->cell_mat[m]]));
+  double dt;
+  if (dt_or_0 > 0) {
+    dt = dt_or_0;
+    if (dt > dz / cmax * (1 + 1e-12)) return fail(MBS_E_INVALID, "dt exceeds the Courant limit dz / c_max");
+  } else {
+    if (!(courant > 0 && courant <= 1)) return fail(MBS_E_INVALID, "courant must be in (0, 1]");
+    dt = courant * dz / cmax;
+  }
+  long long nt = n_steps > 0 ? n_steps : (long long)std::ceil(t_end / dt);
+  if (nt < 1) return fail(MBS_E_INVALID, "no time steps (t_end <= 0 and n_steps <= 0)");
+  if (nt > (1LL << 31)) return fail(MBS_E_INVALID, "too many steps");
+
+  auto s = std::make_unique<mbs_scenario_s>();
+  s->dev = dev;
+  s->dt = dt;
+  s->nt = nt;
+  const int N = std::max(dev->N, 2);
+  s->N = N;
+  s->K = N * N - 1;
+  s->P = N * (N - 1) / 2;
+  const int K = s->K, P = s->P, N2 = N * N;
+  s->ld = ((nx + 2 * mbs::PAD) + 31) / 32 * 32;
+  const int n_mat = (int)dev->mats.size();
+  const double eta0 = std::sqrt(kMu0 / kEps0);
+
+  // EM coefficients (normalised H^ = eta0 H); the extra last material is the
+  // inert pad outside the domain
+  s->emc.assign((size_t)(n_mat + 1) * 4, 0.0);
+  for (int i = 0; i < n_mat; ++i) {
+    const MatDesc &m = dev->mats[i];
+    const double eps = kEps0 * m.eps_r, k = dt * m.sigma / (2 * eps);
+    s->emc[i * 4 + 0] = (1 - k) / (1 + k);
+    s->emc[i * 4 + 1] = (dt / eps) / (1 + k) / (dz * eta0);
+    s->emc[i * 4 + 2] = dt * eta0 / (dz * kMu0 * m.mu_r);
+  }
+  // slots: one per material with a quantum description
+  s->qslot.assign(n_mat + 1, -1);
+  std::vector<int> slot_mat;
+  for (int i = 0; i < n_mat; ++i)
+    if (dev->mats[i].qm >= 0) {
+      s->qslot[i] = (int)slot_mat.size();
+      slot_mat.push_back(i);
+    }
+  s->n_slot = (int)slot_mat.size();
+  s->qstride = mbs::q_stride(N);
+  s->qpar.assign((size_t)std::max(1, s->n_slot) * s->qstride, 0.0);
+  s->zref.assign((size_t)std::max(1, s->n_slot) * N2, 0.0);
+  std::vector<Step> steps(s->n_slot);
+  for (int sl = 0; sl < s->n_slot; ++sl) {
+    const MatDesc &m = dev->mats[slot_mat[sl]];
+    const QDesc &q = dev->qms[m.qm];
+    Step &st = steps[sl];
+    build_step(q, 1.0, dt, st);
+    const double bp = (dt / (kEps0 * m.eps_r)) / (1 + dt * m.sigma / (2 * kEps0 * m.eps_r));
+    const double cpl = bp * m.overlap * q.n3d;
+    double *blk = &s->qpar[(size_t)sl * s->qstride];
+    for (int i = 0; i < K * K; ++i) blk[i] = st.AK[i] - (i % (K + 1) == 0 ? 1.0 : 0.0);
+    for (int i = 0; i < K; ++i) {
+      blk[K * K + i] = st.c[i];
+      blk[K * K + K + i] = cpl * st.g[i];
+    }
+    blk[K * K + 2 * K] = cpl * st.g0;
+    int p = 0;
+    for (int j = 0; j < N; ++j)
+      for (int k = j + 1; k < N; ++k, ++p) {
+        blk[K * K + 2 * K + 1 + p] = (q.lambda[j] - q.lambda[k]) * dt / kHbar;
+        blk[K * K + 2 * K + 1 + P + 2 * p] = q.yref[N + 2 * p];
+        blk[K * K + 2 * K + 1 + P + 2 * p + 1] = q.yref[N + 2 * p + 1];
+      }
+    std::copy(q.yref.begin(), q.yref.end(), &s->zref[(size_t)sl * N2]);
+  }
+
+  for (double v : s->qpar)
+    if (!std::isfinite(v)) return fail(MBS_E_NUMERIC, "non-finite step operator (check H0, mu, rates and dt)");
+
+  // per-cell state and (jittered media) per-cell step operators
+  const int ld = s->ld, off = s->off;
+  s->Dinit.assign((size_t)K * ld, 0.0);
+  s->has_pcell = !dev->jitter.empty() && s->n_slot > 0;
+  if (s->has_pcell) s->pcell.assign((size_t)mbs::pc_rows(N) * ld, 0.0);
+  std::vector<double> d0_slot((size_t)std::max(1, s->n_slot) * K, 0.0);
+  for (int sl = 0; sl < s->n_slot; ++sl) {
+    const QDesc &q = dev->qms[dev->mats[slot_mat[sl]].qm];
+    std::vector<double> x0(N2, 0.0);
+    for (int i = 0; i < N2; ++i)
+      for (int j = 0; j < N2; ++j) x0[i] += steps[sl].Ah[i * N2 + j] * q.yinit[j];
+    for (int i = 0; i < K; ++i) d0_slot[sl * K + i] = x0[full_of(N, i)] - q.yref[full_of(N, i)];
+  }
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : bad)
+  for (int m = 0; m < nx; ++m) {
+    const int mt = dev->cell_mat[m];
+    const int sl = s->qslot[mt];
+    if (sl < 0) continue;
+    if (!s->has_pcell) {
+      for (int i = 0; i < K; ++i) s->Dinit[(size_t)i * ld + off + m] = d0_slot[sl * K + i];
+      continue;
+    }
+    const MatDesc &mm = dev->mats[mt];
+    const QDesc &q = dev->qms[mm.qm];
+    const double fd = dev->jitter[2 * m], fh = dev->jitter[2 * m + 1];
+    Step st;
+    build_step(q, fh, dt, st);
+    const double bp = (dt / (kEps0 * mm.eps_r)) / (1 + dt * mm.sigma / (2 * kEps0 * mm.eps_r));
+    const double cpl = bp * mm.overlap * q.n3d * fd;
+    const size_t col = (size_t)off + m;
+    for (int i = 0; i < K * K; ++i) s->pcell[(size_t)i * ld + col] = st.AK[i] - (i % (K + 1) == 0 ? 1.0 : 0.0);
+    for (int i = 0; i < K; ++i) {
+      s->pcell[(size_t)(K * K + i) * ld + col] = st.c[i];
+      s->pcell[(size_t)(K * K + K + i) * ld + col] = cpl * st.g[i];
+    }
+    s->pcell[(size_t)(K * K + 2 * K) * ld + col] = cpl * st.g0;
+    std::vector<double> x0(N2, 0.0);
+    for (int i = 0; i < N2; ++i)
+      for (int j = 0; j < N2; ++j) x0[i] += st.Ah[i * N2 + j] * q.yinit[j];
+    for (int i = 0; i < K; ++i) s->Dinit[(size_t)i * ld + col] = x0[full_of(N, i)] - q.yref[full_of(N, i)];
+    if (!std::isfinite(st.AK[0])) ++bad;
+  }
+  if (bad) return fail(MBS_E_NUMERIC, "non-finite per-cell propagator");
+
+  // sources
+  for (int k = 0; k < n_src; ++k) {
+    const mbs_source &sr = src[k];
+    if (sr.kind < 0 || sr.kind > 2) return fail(MBS_E_INVALID, "source %d: bad kind", k);
+    if (sr.cell < 2 || sr.cell > nx - 3) return fail(MBS_E_INVALID, "source %d: cell must be in [2, n_cells-3]", k);
+    if (!(sr.tau > 0)) return fail(MBS_E_INVALID, "source %d: tau must be > 0", k);
+    SrcHost h;
+    h.kind = sr.kind;
+    h.cell = sr.cell;
+    h.face = sr.kind == MBS_SRC_TFSF_RIGHT ? sr.cell : (sr.kind == MBS_SRC_TFSF_LEFT ? sr.cell + 1 : -1);
+    h.sH.assign(nt, 0.0);
+    h.sE.assign(nt, 0.0);
+    const MatDesc &ms = dev->mats[dev->cell_mat[sr.cell]];
+    const double cs = light_speed(ms), eta_s = std::sqrt(kMu0 * ms.mu_r / (kEps0 * ms.eps_r));
+    const double bh = s->emc[dev->cell_mat[sr.cell] * 4 + 1];
+    const double ch = h.face >= 0 ? s->emc[dev->cell_mat[h.face] * 4 + 2] : 0.0;
+    auto S = [&](double t) { return sr.e0 / std::cosh((t - sr.t0) / sr.tau) * std::sin(sr.omega * t + sr.phase); };
+    for (long long n = 0; n < nt; ++n) {
+      const double tn = n * dt;
+      if (sr.kind == MBS_SRC_HARD) {
+        h.sE[n] = S(tn + dt);
+      } else {
+        h.sH[n] = (sr.kind == MBS_SRC_TFSF_RIGHT ? -1.0 : 1.0) * ch * S(tn);
+        h.sE[n] = bh * (eta0 / eta_s) * S(tn + 0.5 * dt + 0.5 * dz / cs);
+      }
+    }
+    s->src.push_back(std::move(h));
+  }
+  // boundaries
+  {
+    const double cl = light_speed(dev->mats[dev->cell_mat[0]]), cr = light_speed(dev->mats[dev->cell_mat[nx - 1]]);
+    s->kmur_l = (cl * dt - dz) / (cl * dt + dz);
+    s->kmur_r = (cr * dt - dz) / (cr * dt + dz);
+  }
+  // probes
+  s->pr_coef.assign((size_t)std::max(1, n_probes) * (K + 1), 0.0);
+  for (int k = 0; k < n_probes; ++k) {
+    const mbs_probe &p = probes[k];
+    if (p.cell < 0 || p.cell >= nx) return fail(MBS_E_INVALID, "probe %d: cell out of range", k);
+    if (p.quantity < 0 || p.quantity > 3) return fail(MBS_E_INVALID, "probe %d: bad quantity", k);
+    s->pr_cell.push_back(p.cell);
+    s->pr_q.push_back(p.quantity);
+    if (p.quantity >= 2) {
+      const int mt = dev->cell_mat[p.cell], sl = s->qslot[mt];
+      if (sl < 0) return fail(MBS_E_INVALID, "probe %d: density matrix requested in a cell without medium", k);
+      if (p.i < 0 || p.j < 0 || p.i >= N || p.j >= N) return fail(MBS_E_INVALID, "probe %d: level index", k);
+      const QDesc &q = dev->qms[dev->mats[mt].qm];
+      Step st;
+      build_step(q, dev->jitter.empty() ? 1.0 : dev->jitter[2 * p.cell + 1], dt, st);
+      const std::vector<double> h = rho_functional(q, p.i, p.j, p.quantity == MBS_Q_RHO_IM);
+      std::vector<double> hA(N2, 0.0);   // Ah^T h
+      for (int c = 0; c < N2; ++c)
+        for (int r = 0; r < N2; ++r) hA[c] += h[r] * st.Ah[r * N2 + c];
+      double h0 = 0;
+      for (int c = 0; c < N2; ++c) h0 += hA[c] * q.yref[c];
+      double *co = &s->pr_coef[(size_t)k * (K + 1)];
+      for (int i = 0; i < K; ++i) co[i] = hA[full_of(N, i)] - (i < N - 1 ? hA[N - 1] : 0.0);
+      co[K] = h0;
+    }
+  }
+  // cells for the state check: probes plus a strided sample of media
+  {
+    std::vector<int> med;
+    for (int m = 0; m < nx; ++m)
+      if (s->qslot[dev->cell_mat[m]] >= 0) med.push_back(m);
+    const size_t want = 4096;
+    const size_t stride = std::max<size_t>(1, med.size() / want);
+    for (size_t i = 0; i < med.size(); i += stride) s->chk_cells.push_back(med[i]);
+    for (int c : s->pr_cell) s->chk_cells.push_back(c);
+  }
+
+  // device-resident tables shared by both precisions
+  cudaError_t e = cudaGetDevice(&s->device_id);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  g_h2d = &s->h2d_bytes;
+  std::vector<uint8_t> matpad(ld, (uint8_t)n_mat);
+  for (int m = 0; m < nx; ++m) matpad[off + m] = dev->cell_mat[m];
+  int rc;
+  if ((rc = upload_raw(matpad, &s->d_mat)) || (rc = upload_raw(s->qslot, &s->d_qslot)) ||
+      (rc = upload_raw(s->pr_cell, &s->d_pr_cell)) || (rc = upload_raw(s->pr_q, &s->d_pr_q)) ||
+      (rc = upload_raw(s->chk_cells, &s->d_chk_cells)) || (rc = upload_raw(s->zref, &s->d_zref))) {
+    g_h2d = nullptr;
+    free_scenario(s.get());
+    return rc;
+  }
+  g_h2d = nullptr;
+  const size_t nchk = std::max<size_t>(1, s->chk_cells.size());
+  if ((e = cudaMalloc(&s->d_flags, 4 * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_chk_min, nchk * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_chk_tr, nchk * sizeof(double))) != cudaSuccess) {
+    free_scenario(s.get());
+    return cuda_fail(e, "cudaMalloc");
+  }
+  *out = s.release();
+  return MBS_OK;
+}
+
+void mbs_scenario_destroy(mbs_scenario_t s) {
+  if (!s) return;
+  free_scenario(s);
+  delete s;
+}
+
+int mbs_scenario_info(mbs_scenario_t s, double *dt, double *dz, long long *n_steps) {
+  if (!s) return fail(MBS_E_INVALID, "scenario is NULL");
+  if (dt) *dt = s->dt;
+  if (dz) *dz = s->dev->dz;
+  if (n_steps) *n_steps = s->nt;
+  return MBS_OK;
+}
+
+static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
+  const int prec = o.precision;
+  g_h2d = &s->h2d_bytes;
+  int rc = ensure_bundle(s, prec);
+  g_h2d = nullptr;
+  if (rc) return rc;
+  s->d2h_bytes = 0;
+  s->launches = 0;
+  Bundle &b = s->b[prec];
+  const size_t row = (size_t)s->ld * b.rb;
+  const int K = s->K;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    if ((e = cudaMemsetAsync(b.E[i], 0, row, st)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(b.H[i], 0, row, st)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(b.C[i], 0, row * K, st)) != cudaSuccess) break;
+    e = cudaMemcpyAsync(b.D[i], b.Dinit, row * K, cudaMemcpyDeviceToDevice, st);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.pd, 0, row, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_flags, 0, 4 * sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "state reset");
+  mbs::Args a = make_args(s, prec);
+
+  int algo = o.algo;
+  if (algo == MBS_ALGO_AUTO) algo = mbs::tiled_supported(prec, s->N) && (!s->has_pcell || s->N == 2) ? MBS_ALGO_TILED : MBS_ALGO_PLAIN;
+  int T = o.tile_steps > 0 ? o.tile_steps : 16;
+  const int chk = o.check_every > 0 ? o.check_every : 0;
+  const int nchk = (int)s->chk_cells.size();
+  int cur = 0;
+  auto check = [&](int c) -> int {
+    if (!nchk) return 0;
+    ++s->launches;
+    return mbs::launch_check(a, c, s->d_chk_cells, nchk, s->d_chk_min, s->d_chk_tr, s->d_zref, nullptr, st);
+  };
+  if (algo == MBS_ALGO_TILED) {
+    if (!mbs::tiled_supported(prec, s->N) || (s->has_pcell && s->N != 2))
+      return fail(MBS_E_INVALID, "tiled kernels cover N = 2 (also with per-cell factors) and N = 3");
+    const int R = s->N == 2 ? 4 : 2;
+    if (T % 4 != 0 || T < 4 || 32 * R - 2 * T < 8)
+      return fail(MBS_E_INVALID, "tile_steps must be a multiple of 4 in [4, %d]", (32 * R - 8) / 2);
+    // each lane's R-cell group must hold at most one medium material
+    for (int g = 0; g * R < s->dev->nx; ++g) {
+      int sl = -1;
+      for (int j = 0; j < R && g * R + j < s->dev->nx; ++j) {
+        const int q = s->qslot[s->dev->cell_mat[g * R + j]];
+        if (q >= 0 && sl >= 0 && q != sl)
+          return fail(MBS_E_INVALID, "two media meet inside a %d-cell group; use the plain algorithm", R);
+        if (q >= 0) sl = q;
+      }
+    }
+    long long done = 0;
+    while (done < s->nt) {
+      const int ns = (int)std::min<long long>(T, s->nt - done);
+      int r = mbs::launch_tiled(a, done, ns, T, cur, st);
+      ++s->launches;
+      if (r) return cuda_fail((cudaError_t)r, "tiled launch");
+      cur ^= 1;
+      done += ns;
+      if (chk && done < s->nt && (done / chk) != ((done - ns) / chk))
+        if ((r = check(cur))) return cuda_fail((cudaError_t)r, "check launch");
+    }
+  } else {
+    for (long long n = 0; n < s->nt; ++n) {
+      int r = mbs::launch_plain_step(a, n, cur, st);
+      s->launches += 2;
+      if (r) return cuda_fail((cudaError_t)r, "plain launch");
+      cur ^= 1;
+      if (chk && (n + 1) % chk == 0 && n + 1 < s->nt)
+        if ((r = check(0))) return cuda_fail((cudaError_t)r, "check launch");
+    }
+  }
+  // plain: D, H live in buffer 0, E in `cur`; tiled: everything in `cur`
+  const int dcur = algo == MBS_ALGO_TILED ? cur : 0;
+  if ((rc = check(dcur))) return cuda_fail((cudaError_t)rc, "check launch");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "solve");
+  s->solved_prec = prec;
+  s->last_cur = cur;
+  s->steps_run = s->nt;
+  int flags[4] = {0, 0, 0, 0};
+  if ((e = cudaMemcpy(flags, s->d_flags, sizeof flags, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "flags");
+  s->d2h_bytes += sizeof flags + (long long)nchk * 2 * sizeof(double);
+  s->st_min = 1e300;
+  s->st_trace = 0;
+  if (nchk) {
+    std::vector<double> mn(nchk), tr(nchk);
+    if ((e = cudaMemcpy(mn.data(), s->d_chk_min, nchk * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(tr.data(), s->d_chk_tr, nchk * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "check results");
+    for (int i = 0; i < nchk; ++i) {
+      s->st_min = std::min(s->st_min, mn[i]);
+      s->st_trace = std::max(s->st_trace, tr[i]);
+    }
+  } else {
+    s->st_min = 0;
+  }
+  if (flags[0]) return fail(MBS_E_NUMERIC, "non-finite density matrix");
+  if (nchk && s->st_min < -1e-6) return fail(MBS_E_NUMERIC, "density matrix eigenvalue %.3g < -1e-6", s->st_min);
+  return MBS_OK;
+}
+
+int mbs_solve(mbs_scenario_t *batch, int n_scen, const mbs_opts *opts, void *cuda_stream) {
+  g_err.clear();
+  if (!batch || n_scen < 1) return fail(MBS_E_INVALID, "empty batch");
+  mbs_opts o{MBS_PREC_FP32, MBS_ALGO_AUTO, 0, 0};
+  if (opts) o = *opts;
+  if (o.precision != MBS_PREC_FP64 && o.precision != MBS_PREC_FP32) return fail(MBS_E_INVALID, "bad precision");
+  if (o.algo < 0 || o.algo > 2) return fail(MBS_E_INVALID, "bad algorithm");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  for (int i = 0; i < n_scen; ++i) {
+    if (!batch[i]) return fail(MBS_E_INVALID, "scenario %d is NULL", i);
+    const int rc = solve_one(batch[i], o, st);
+    if (rc) return rc;
+  }
+  return MBS_OK;
+}
+
+int mbs_fetch_records(mbs_scenario_t s, int probe, double *out, size_t cap, size_t *n_written) {
+  g_err.clear();
+  if (!s) return fail(MBS_E_INVALID, "scenario is NULL");
+  if (probe < 0 || probe >= (int)s->pr_cell.size()) return fail(MBS_E_INVALID, "probe index out of range");
+  const size_t n = (size_t)s->nt;
+  if (n_written) *n_written = n;
+  if (!out) return MBS_OK;
+  if (cap < n) return fail(MBS_E_INVALID, "capacity %zu < %zu", cap, n);
+  if (s->solved_prec < 0) return fail(MBS_E_STATE, "no solve has run");
+  const Bundle &b = s->b[s->solved_prec];
+  const double scale = s->pr_q[probe] == MBS_Q_H ? 1.0 / std::sqrt(kMu0 / kEps0) : 1.0;
+  cudaError_t e;
+  if (s->solved_prec == 0) {
+    e = cudaMemcpy(out, (const double *)b.rec + (size_t)probe * n, n * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "fetch");
+    s->d2h_bytes += (long long)(n * sizeof(double));
+    if (scale != 1.0)
+      for (size_t i = 0; i < n; ++i) out[i] *= scale;
+  } else {
+    std::vector<float> f(n);
+    e = cudaMemcpy(f.data(), (const float *)b.rec + (size_t)probe * n, n * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "fetch");
+    s->d2h_bytes += (long long)(n * sizeof(float));
+    for (size_t i = 0; i < n; ++i) out[i] = scale * (double)f[i];
+  }
+  return MBS_OK;
+}
+
+int mbs_scenario_counters(mbs_scenario_t s, long long *h2d_bytes, long long *d2h_bytes, long long *kernel_launches) {
+  g_err.clear();
+  if (!s) return fail(MBS_E_INVALID, "scenario is NULL");
+  if (h2d_bytes) *h2d_bytes = s->h2d_bytes;
+  if (d2h_bytes) *d2h_bytes = s->d2h_bytes;
+  if (kernel_launches) *kernel_launches = s->launches;
+  return MBS_OK;
+}
+
+int mbs_scenario_stats(mbs_scenario_t s, double *max_trace_dev, double *min_eig, long long *n_steps) {
+  g_err.clear();
+  if (!s) return fail(MBS_E_INVALID, "scenario is NULL");
+  if (s->solved_prec < 0) return fail(MBS_E_STATE, "no solve has run");
+  if (max_trace_dev) *max_trace_dev = s->st_trace;
+  if (min_eig) *min_eig = s->st_min;
+  if (n_steps) *n_steps = s->steps_run;
+  return MBS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// mbs_internal.h -- private interface between the host setup (mbs_host.cpp)
+// and the CUDA kernels (mbs_kernels.cu) of the Maxwell-Bloch hot path.
+//
+// State representation on the device (per medium cell):
+//   * the density matrix after the first half of the constant propagator,
+//     x^n = exp(L0 dt/2) rho^{n-1/2}, in real coordinates of the dipole
+//     eigenbasis (rho~ = V^+ rho V): populations rho~_kk (k < N-1) and the
+//     (Re, Im) pairs of rho~_jk, j < k -- K = N^2 - 1 numbers;
+//   * stored as the deviation delta = x - x_ref from a reference state
+//     (the steady state of L0 when unique, else the initial state), so that
+//     near-unity populations keep their low-order bits in FP32;
+//   * in FP32, a Kahan compensation word per component.
+// One time step (Strang splitting with adjacent half steps merged):
+//   v = R(E^n) x  (exact field propagator: rotation of each coherence pair by
+//                  theta_p = kappa_p E^n, populations unchanged)
+//   u = v - x_ref = delta + (R - 1) x
+//   delta' = A u + c          (A = exp(L0 dt) on deviations, c its offset)
+//   d_t P^{n+1/2} = n3D (g . u + g0)  (tr{mu L0 exp(L0 dt/2) v})
+//   E^{n+1} = a E^n - b' Gamma d_t P + b' (H_{m+1} - H_m)/dz
+// Fields: E in V/m; H is stored normalised, H^ = eta0 H (V/m), so that in
+// vacuum at Courant number 1 both field coefficients are exactly 1.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace mbs {
+
+constexpr int NMAX = 6;
+constexpr int MAXSRC = 4;
+constexpr int MAXPROBE = 64;
+constexpr int PAD = 256;  // left/right margin cells of every cell array
+
+// Packed per-quantum-material parameter block (in the state's real type):
+//   am1[K*K] (A - I, row-major) | c[K] | w[K] | w0 | kap[P] | zr[2P]
+// w, w0 already include b' Gamma n3D, i.e. E -= w . u + w0 [V/m].
+inline int q_k(int N) { return N * N - 1; }
+inline int q_p(int N) { return N * (N - 1) / 2; }
+inline int q_stride(int N) {
+  int K = q_k(N), P = q_p(N);
+  return K * K + 2 * K + 1 + 3 * P;
+}
+// Per-cell parameter rows (cells with their own propagator): am1, c, w, w0.
+inline int pc_rows(int N) {
+  int K = q_k(N);
+  return K * K + 2 * K + 1;
+}
+
+struct SrcDev {
+  int kind;         // 0 TF/SF +x, 1 TF/SF -x, 2 hard
+  int face;         // face receiving the H correction (-1: none)
+  int cell;         // cell receiving the E correction / hard value
+  int pad_;
+  const void *sH;   // [nt] H^ correction per step (added at `face`)
+  const void *sE;   // [nt] E correction (or hard value) per step
+};
+
+// Everything a launch needs (passed by value).
+struct Args {
+  int prec;                    // 0 = FP64, 1 = FP32
+  int N, K, P;
+  int nx, ld, off;             // cells, padded row length, index of cell 0
+  long long nt;                // total steps of the scenario
+  void *E[2], *H[2];           // [ld] ping-pong (plain path updates H in place in H[0])
+  void *D[2], *C[2];           // [K][ld] deviation / Kahan compensation
+  void *pd;                    // [ld] coupling term of the plain path
+  const uint8_t *mat;          // [ld] material id per cell (pad cells: n_mat)
+  int n_mat_all;               // materials incl. the pad material
+  const void *emc;             // [n_mat_all][4]: a, b^, c^, 0
+  const int *qslot;            // [n_mat_all]: parameter slot or -1
+  const void *qpar;            // [n_slot][qstride]
+  int n_slot, qstride;
+  const void *pcell;           // [pc_rows][ld] per-cell parameters or null
+  int n_src;
+  SrcDev src[MAXSRC];
+  int bc_l, bc_r;              // 0 = Mur, 1 = PEC
+  double kmur_l, kmur_r;
+  int n_probe;
+  const int *pr_cell;          // [n_probe]
+  const int *pr_q;             // [n_probe] quantity
+  const void *pr_coef;         // [n_probe][K+1]: rho probes h_K, h0
+  void *rec;                   // [n_probe][nt]
+  int *flags;                  // [4] device status words
+};
+
+// Launchers (mbs_kernels.cu).  All return 0 or a cudaError_t value.
+int launch_plain_step(const Args &a, long long n, int cur, void *stream);
+int launch_tiled(const Args &a, long long n0, int nsteps, int T, int cur, void *stream);
+int tiled_supported(int prec, int N);
+int launch_check(const Args &a, int cur, const int *cells, int n_cells, double *out_min_eig,
+                 double *out_trace_dev, const void *zref_full, const void *V, void *stream);
+
+}  // namespace mbs

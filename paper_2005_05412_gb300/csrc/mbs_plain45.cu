@@ -1,0 +1,28 @@
+// mbs_plain45.cu -- plain (Algorithm 1) step and state check for N in {4, 5}.
+#include "mbs_device.cuh"
+
+namespace mbs {
+using namespace dev;
+
+int plain_step_n45(int N, const Args &a, long long n, int cur, cudaStream_t st) {
+  switch (N) {
+    case 4:
+      return a.prec == 0 ? plain_step_impl<double, 4, false>(a, n, cur, st) : plain_step_impl<float, 4, true>(a, n, cur, st);
+    case 5:
+      return a.prec == 0 ? plain_step_impl<double, 5, false>(a, n, cur, st) : plain_step_impl<float, 5, true>(a, n, cur, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+int check_n45(int N, const Args &a, int cur, const int *cells, int n_cells, double *mn, double *tr,
+              const double *z, cudaStream_t st) {
+  switch (N) {
+    case 4:
+      return a.prec == 0 ? check_impl<double, 4>(a, cur, cells, n_cells, mn, tr, z, st) : check_impl<float, 4>(a, cur, cells, n_cells, mn, tr, z, st);
+    case 5:
+      return a.prec == 0 ? check_impl<double, 5>(a, cur, cells, n_cells, mn, tr, z, st) : check_impl<float, 5>(a, cur, cells, n_cells, mn, tr, z, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace mbs
