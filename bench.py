@@ -149,6 +149,8 @@ def run_ours(args, rank, world, local):
     dev_index = torch.cuda.current_device()
     stream = torch.cuda.Stream()
     p = workload(args.workload)
+    if args.nsteps > 0:
+        p = p.replace(n_steps=args.nsteps)
     cell_steps = p.n_cells * p.n_steps
     dev = mbs.device_from_problem(p)
     sc = mbs.scenario_from_problem(dev, p)
@@ -319,6 +321,7 @@ def main():
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--quick", action="store_true", help="skip the FP64, e2e and CPU legs")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--nsteps", type=int, default=0, help="override the workload's step count (profiling)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

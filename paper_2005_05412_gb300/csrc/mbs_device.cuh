@@ -20,6 +20,7 @@
 //    neighbouring warps' halo reads race-free.  No shared-memory traffic or
 //    block barrier happens inside the time loop.
 //
+// In FP32 the fields are float-float pairs (see "fields" below).
 // The field rotation needs sin(theta) and cos(theta) - 1 of small angles to
 // full relative precision; they come from their Taylor series (coefficients
 // +-1/n!) for |theta| <= 1/2 and from the CUDA math library otherwise.
@@ -204,6 +205,67 @@ __device__ __forceinline__ real probe_rho(const real *coef, const real (&u)[N * 
   return v;
 }
 
+// ------------------------------------------------------------- fields
+// FP64: a field value is one double.  FP32: a field value is an unevaluated
+// pair hi + lo of floats (float-float), updated with error-free
+// transformations: a single FP32 word rounds |E| ~ 1e9 V/m to ~100 V/m every
+// step, and a high-Q resonant medium integrates those errors into its
+// polarisation, so single-word FP32 fields drift by ~1e-3 relative within a
+// few thousand steps while float-float fields track FP64 to ~1e-7.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+// (h, l) += (a, b), renormalised
+__device__ __forceinline__ void ff_add(float &h, float &l, float a, float b) {
+  float s, e;
+  two_sum(h, a, s, e);
+  e += l + b;
+  h = s + e;
+  l = e - (h - s);
+}
+
+// f += c (xr - xl) + extra   (extra: a small correction added to the low part)
+template <typename real>
+__device__ __forceinline__ void fld_axpy_diff(real &fh, real &fl, real c, real xrh, real xrl, real xlh, real xll,
+                                              real extra) {
+  if constexpr (sizeof(real) == 8) {
+    fh += c * (xrh - xlh) + extra;
+  } else {
+    float dh, de, ph, pe;
+    two_sum(xrh, -xlh, dh, de);
+    const float dl = de + (xrl - xll);
+    two_prod(c, dh, ph, pe);
+    ff_add(fh, fl, ph, pe + c * dl + extra);
+  }
+}
+
+// source table entry n: FP64 [nt]; FP32 [2][nt] (hi row, lo row)
+template <typename real>
+__device__ __forceinline__ void src_val(const void *tab, long long n, long long nt, real &h, real &l) {
+  const real *t = reinterpret_cast<const real *>(tab);
+  h = t[n];
+  l = sizeof(real) == 8 ? real(0) : t[nt + n];
+}
+
+template <typename real>
+__device__ __forceinline__ void fld_add(real &fh, real &fl, real h, real l) {
+  if constexpr (sizeof(real) == 8)
+    fh += h;
+  else
+    ff_add(fh, fl, h, l);
+}
+
+template <typename real>
+__device__ __forceinline__ real fld_val(real h, real l) {
+  return sizeof(real) == 8 ? h : h + l;
+}
+
 template <typename real>
 __device__ __forceinline__ real emc_at(const Args &a, int idx, int k) {
   return reinterpret_cast<const real *>(a.emc)[a.mat[idx] * 4 + k];
@@ -214,16 +276,27 @@ __device__ __forceinline__ real emc_at(const Args &a, int idx, int k) {
 template <typename real, int N, bool KAHAN>
 __global__ void k_plain_a(const Args a, long long n, int cur) {
   constexpr int K = N * N - 1;
+  constexpr bool FF = sizeof(real) == 4;
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= a.nx) return;
   const int idx = a.off + m;
   const real *E = reinterpret_cast<const real *>(a.E[cur]);
+  const real *El = reinterpret_cast<const real *>(a.El[cur]);
   real *H = reinterpret_cast<real *>(a.H[0]);
+  real *Hl = reinterpret_cast<real *>(a.Hl[0]);
+  const real e_here = fld_val<real>(E[idx], FF ? El[idx] : real(0));
   if (m >= 1) {
-    real h = H[idx] + emc_at<real>(a, idx, 2) * (E[idx] - E[idx - 1]);
+    real hh = H[idx], hl = FF ? Hl[idx] : real(0);
+    fld_axpy_diff<real>(hh, hl, emc_at<real>(a, idx, 2), E[idx], FF ? El[idx] : real(0), E[idx - 1],
+                        FF ? El[idx - 1] : real(0), real(0));
     for (int s = 0; s < a.n_src; ++s)
-      if (a.src[s].face == m) h += reinterpret_cast<const real *>(a.src[s].sH)[n];
-    H[idx] = h;
+      if (a.src[s].face == m) {
+        real sh, sl;
+        src_val<real>(a.src[s].sH, n, a.nt, sh, sl);
+        fld_add<real>(hh, hl, sh, sl);
+      }
+    H[idx] = hh;
+    if (FF) Hl[idx] = hl;
   }
   real *pd = reinterpret_cast<real *>(a.pd);
   const int slot = a.qslot[a.mat[idx]];
@@ -243,10 +316,10 @@ __global__ void k_plain_a(const Args a, long long n, int cur) {
   real pw;
   if (a.pcell) {
     PrmCell<real, N> q{reinterpret_cast<const real *>(a.pcell) + idx, a.ld, mb};
-    pw = bloch_step<real, N, KAHAN>(q, E[idx], d, cc, u);
+    pw = bloch_step<real, N, KAHAN>(q, e_here, d, cc, u);
   } else {
     PrmBlock<real, N> q{mb};
-    pw = bloch_step<real, N, KAHAN>(q, E[idx], d, cc, u);
+    pw = bloch_step<real, N, KAHAN>(q, e_here, d, cc, u);
   }
 #pragma unroll
   for (int i = 0; i < K; ++i) {
@@ -260,57 +333,71 @@ __global__ void k_plain_a(const Args a, long long n, int cur) {
           probe_rho<real, N>(reinterpret_cast<const real *>(a.pr_coef) + (size_t)p * (K + 1), u);
 }
 
+// E^{n+1} of cell m (before boundary conditions): returns (h, l)
 template <typename real>
-__device__ __forceinline__ real e_update(const Args &a, const real *E, const real *H, const real *pd,
-                                         int m, long long n, bool *hard) {
+__device__ __forceinline__ void e_update(const Args &a, int cur, const real *pd, int m, long long n, real &eh,
+                                         real &el) {
+  constexpr bool FF = sizeof(real) == 4;
   const int idx = a.off + m;
-  real e = emc_at<real>(a, idx, 0) * E[idx] - pd[idx] + emc_at<real>(a, idx, 1) * (H[idx + 1] - H[idx]);
+  const real *E = reinterpret_cast<const real *>(a.E[cur]);
+  const real *Elo = reinterpret_cast<const real *>(a.El[cur]);
+  const real *H = reinterpret_cast<const real *>(a.H[0]);
+  const real *Hlo = reinterpret_cast<const real *>(a.Hl[0]);
+  eh = E[idx];
+  el = FF ? Elo[idx] : real(0);
+  const real extra = emc_at<real>(a, idx, 0) * eh - pd[idx];   // (a' - 1) E - coupling
+  fld_axpy_diff<real>(eh, el, emc_at<real>(a, idx, 1), H[idx + 1], FF ? Hlo[idx + 1] : real(0), H[idx],
+                      FF ? Hlo[idx] : real(0), extra);
   for (int s = 0; s < a.n_src; ++s)
     if (a.src[s].cell == m) {
-      const real v = reinterpret_cast<const real *>(a.src[s].sE)[n];
+      real vh, vl;
+      src_val<real>(a.src[s].sE, n, a.nt, vh, vl);
       if (a.src[s].kind == 2) {
-        e = v;
-        *hard = true;
+        eh = vh;
+        el = vl;
       } else {
-        e += v;
+        fld_add<real>(eh, el, vh, vl);
       }
     }
-  return e;
 }
 
-// Launch B of step n: E^{n+1} into E[cur ^ 1], sources, boundaries, records.
+// Launch B of step n: E^{n+1} into buffers cur ^ 1, sources, boundaries, records.
 template <typename real>
 __global__ void k_plain_b(const Args a, long long n, int cur) {
+  constexpr bool FF = sizeof(real) == 4;
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= a.nx) return;
   const int idx = a.off + m;
   const real *E = reinterpret_cast<const real *>(a.E[cur]);
+  const real *Elo = reinterpret_cast<const real *>(a.El[cur]);
   real *En = reinterpret_cast<real *>(a.E[cur ^ 1]);
-  const real *H = reinterpret_cast<const real *>(a.H[0]);
+  real *Eln = reinterpret_cast<real *>(a.El[cur ^ 1]);
   const real *pd = reinterpret_cast<const real *>(a.pd);
-  bool hard = false;
-  real e = e_update<real>(a, E, H, pd, m, n, &hard);
-  if (m == 0 && a.nx > 1) {
-    if (a.bc_l == 1) {
-      e = real(0);
+  real eh, el;
+  e_update<real>(a, cur, pd, m, n, eh, el);
+  const bool left = m == 0, right = m == a.nx - 1;
+  if (left || right) {
+    const int nb = left ? 1 : m - 1;            // interior neighbour
+    if ((left ? a.bc_l : a.bc_r) == 1) {
+      eh = el = real(0);
     } else {
-      bool h2 = false;
-      const real e1 = e_update<real>(a, E, H, pd, 1, n, &h2);
-      e = E[idx + 1] + real(a.kmur_l) * (e1 - E[idx]);
-    }
-  } else if (m == a.nx - 1 && a.nx > 1) {
-    if (a.bc_r == 1) {
-      e = real(0);
-    } else {
-      bool h2 = false;
-      const real e1 = e_update<real>(a, E, H, pd, m - 1, n, &h2);
-      e = E[idx - 1] + real(a.kmur_r) * (e1 - E[idx]);
+      real nh, nl;                              // neighbour's E^{n+1}
+      e_update<real>(a, cur, pd, nb, n, nh, nl);
+      // E_b^{n+1} = E_nb^n + k (E_nb^{n+1} - E_b^n)
+      eh = E[a.off + nb];
+      el = FF ? Elo[a.off + nb] : real(0);
+      fld_axpy_diff<real>(eh, el, real(left ? a.kmur_l : a.kmur_r), nh, nl, E[idx], FF ? Elo[idx] : real(0),
+                          real(0));
     }
   }
-  En[idx] = e;
+  En[idx] = eh;
+  if (FF) Eln[idx] = el;
+  const real *H = reinterpret_cast<const real *>(a.H[0]);
+  const real *Hlo = reinterpret_cast<const real *>(a.Hl[0]);
   for (int p = 0; p < a.n_probe; ++p)
     if (a.pr_cell[p] == m && a.pr_q[p] < 2)
-      reinterpret_cast<real *>(a.rec)[(size_t)p * a.nt + n] = a.pr_q[p] == 0 ? e : H[idx];
+      reinterpret_cast<real *>(a.rec)[(size_t)p * a.nt + n] =
+          a.pr_q[p] == 0 ? fld_val<real>(eh, el) : fld_val<real>(H[idx], FF ? Hlo[idx] : real(0));
 }
 
 // ========================================================= tiled path
@@ -323,6 +410,11 @@ template <>
 __device__ __forceinline__ void ld_row<float, 4>(const float *p, float (&v)[4]) {
   const float4 t = *reinterpret_cast<const float4 *>(p);
   v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+template <>
+__device__ __forceinline__ void ld_row<float, 2>(const float *p, float (&v)[2]) {
+  const float2 t = *reinterpret_cast<const float2 *>(p);
+  v[0] = t.x; v[1] = t.y;
 }
 template <>
 __device__ __forceinline__ void ld_row<double, 2>(const double *p, double (&v)[2]) {
@@ -345,6 +437,10 @@ __device__ __forceinline__ void st_row<float, 4>(float *p, const float (&v)[4]) 
   *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 template <>
+__device__ __forceinline__ void st_row<float, 2>(float *p, const float (&v)[2]) {
+  *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+template <>
 __device__ __forceinline__ void st_row<double, 2>(double *p, const double (&v)[2]) {
   *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
 }
@@ -361,6 +457,7 @@ __device__ __forceinline__ void st_row<double, 4>(double *p, const double (&v)[4
 template <typename real, int N, int R, bool KAHAN, bool PERCELL>
 __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int nsteps, int T, int cur) {
   constexpr int K = N * N - 1;
+  constexpr bool FF = sizeof(real) == 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real *s_emc = reinterpret_cast<real *>(smem_raw);
   real *s_q = s_emc + a.n_mat_all * 4;
@@ -379,15 +476,19 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
   const int g0 = tb + lane * R;         // first cell of this lane
   const int base = a.off + g0;          // its array index (>= 0, multiple of R)
 
-  const real *Ein = reinterpret_cast<const real *>(a.E[cur]);
-  const real *Hin = reinterpret_cast<const real *>(a.H[cur]);
+  real E[R], El[R], H[R], Hl[R], ca[R], cb[R], ch[R];
+  real d[K][R], cc[K][R];
+  ld_row<real, R>(reinterpret_cast<const real *>(a.E[cur]) + base, E);
+  ld_row<real, R>(reinterpret_cast<const real *>(a.H[cur]) + base, H);
+  if (FF) {
+    ld_row<real, R>(reinterpret_cast<const real *>(a.El[cur]) + base, El);
+    ld_row<real, R>(reinterpret_cast<const real *>(a.Hl[cur]) + base, Hl);
+  } else {
+#pragma unroll
+    for (int j = 0; j < R; ++j) El[j] = Hl[j] = real(0);
+  }
   const real *Din = reinterpret_cast<const real *>(a.D[cur]);
   const real *Cin = reinterpret_cast<const real *>(a.C[cur]);
-
-  real E[R], H[R], ca[R], cb[R], ch[R];
-  real d[K][R], cc[K][R];
-  ld_row<real, R>(Ein + base, E);
-  ld_row<real, R>(Hin + base, H);
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     ld_row<real, R>(Din + (size_t)i * a.ld + base, d[i]);
@@ -450,16 +551,25 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
   for (int t = 0; t < nsteps; ++t) {
     const long long n = n0 + t;
     // ---- H^{n+1/2} on the left faces of my cells
-    const real el = __shfl_up_sync(FULL, E[R - 1], 1);
-    real Hn[R];
+    const real elh = __shfl_up_sync(FULL, E[R - 1], 1);
+    const real ell = FF ? __shfl_up_sync(FULL, El[R - 1], 1) : real(0);
+    real Hn[R], Hln[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) Hn[j] = H[j] + ch[j] * (E[j] - (j ? E[j - 1] : el));
+    for (int j = 0; j < R; ++j) {
+      Hn[j] = H[j];
+      Hln[j] = Hl[j];
+      fld_axpy_diff<real>(Hn[j], Hln[j], ch[j], E[j], El[j], j ? E[j - 1] : elh, j ? El[j - 1] : ell, real(0));
+    }
     if (any_src) {
       for (int s = 0; s < a.n_src; ++s) {
         const int f = a.src[s].face - g0;
 #pragma unroll
         for (int j = 0; j < R; ++j)
-          if (f == j) Hn[j] += reinterpret_cast<const real *>(a.src[s].sH)[n];
+          if (f == j) {
+            real vh, vl;
+            src_val<real>(a.src[s].sH, n, a.nt, vh, vl);
+            fld_add<real>(Hn[j], Hln[j], vh, vl);
+          }
       }
     }
     // ---- rho^{n+1/2} and the coupling term
@@ -474,10 +584,11 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
           dj[i] = d[i][j];
           cj[i] = cc[i][j];
         }
+        const real ej = fld_val<real>(E[j], El[j]);
         if (PERCELL)
-          pw[j] = bloch_step<real, N, KAHAN>(pr[PERCELL ? j : 0], E[j], dj, cj, u);
+          pw[j] = bloch_step<real, N, KAHAN>(pr[PERCELL ? j : 0], ej, dj, cj, u);
         else
-          pw[j] = bloch_step<real, N, KAHAN>(PrmBlock<real, N>{mb}, E[j], dj, cj, u);
+          pw[j] = bloch_step<real, N, KAHAN>(PrmBlock<real, N>{mb}, ej, dj, cj, u);
 #pragma unroll
         for (int i = 0; i < K; ++i) {
           d[i][j] = dj[i];
@@ -491,44 +602,75 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
       }
     }
     // ---- E^{n+1}
-    const real hr = __shfl_down_sync(FULL, Hn[0], 1);
-    real En[R];
+    const real hrh = __shfl_down_sync(FULL, Hn[0], 1);
+    const real hrl = FF ? __shfl_down_sync(FULL, Hln[0], 1) : real(0);
+    real En[R], Eln[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) En[j] = ca[j] * E[j] - pw[j] + cb[j] * ((j < R - 1 ? Hn[j + 1] : hr) - Hn[j]);
+    for (int j = 0; j < R; ++j) {
+      En[j] = E[j];
+      Eln[j] = El[j];
+      fld_axpy_diff<real>(En[j], Eln[j], cb[j], j < R - 1 ? Hn[j + 1] : hrh, j < R - 1 ? Hln[j + 1] : hrl, Hn[j],
+                          Hln[j], ca[j] * E[j] - pw[j]);
+    }
     if (any_src) {
       for (int s = 0; s < a.n_src; ++s) {
         const int c = a.src[s].cell - g0;
 #pragma unroll
         for (int j = 0; j < R; ++j)
           if (c == j) {
-            const real v = reinterpret_cast<const real *>(a.src[s].sE)[n];
-            En[j] = a.src[s].kind == 2 ? v : En[j] + v;
+            real vh, vl;
+            src_val<real>(a.src[s].sE, n, a.nt, vh, vl);
+            if (a.src[s].kind == 2) {
+              En[j] = vh;
+              Eln[j] = vl;
+            } else {
+              fld_add<real>(En[j], Eln[j], vh, vl);
+            }
           }
       }
     }
     if (any_bnd) {
-      const real ero = __shfl_down_sync(FULL, E[0], 1);
-      const real ern = __shfl_down_sync(FULL, En[0], 1);
-      const real elo = __shfl_up_sync(FULL, E[R - 1], 1);
-      const real eln = __shfl_up_sync(FULL, En[R - 1], 1);
-      real Eb[R];
-#pragma unroll
-      for (int j = 0; j < R; ++j) Eb[j] = En[j];
+      // neighbours' old and new E across lane borders
+      const real r_oh = __shfl_down_sync(FULL, E[0], 1), r_ol = __shfl_down_sync(FULL, El[0], 1);
+      const real r_nh = __shfl_down_sync(FULL, En[0], 1), r_nl = __shfl_down_sync(FULL, Eln[0], 1);
+      const real l_oh = __shfl_up_sync(FULL, E[R - 1], 1), l_ol = __shfl_up_sync(FULL, El[R - 1], 1);
+      const real l_nh = __shfl_up_sync(FULL, En[R - 1], 1), l_nl = __shfl_up_sync(FULL, Eln[R - 1], 1);
+      real Bh[R], Bl[R];
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        if (g0 + j == 0) {
-          const real e1o = j < R - 1 ? E[j + 1] : ero;
-          const real e1n = j < R - 1 ? En[j + 1] : ern;
-          Eb[j] = a.bc_l == 1 ? real(0) : e1o + real(a.kmur_l) * (e1n - E[j]);
-        }
-        if (g0 + j == a.nx - 1) {
-          const real e1o = j ? E[j - 1] : elo;
-          const real e1n = j ? En[j - 1] : eln;
-          Eb[j] = a.bc_r == 1 ? real(0) : e1o + real(a.kmur_r) * (e1n - E[j]);
+        Bh[j] = En[j];
+        Bl[j] = Eln[j];
+      }
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const bool lft = g0 + j == 0, rgt = g0 + j == a.nx - 1;
+        if (lft || rgt) {
+          real oh, ol, nh, nl;
+          if (lft) {
+            oh = j < R - 1 ? E[j + 1] : r_oh;
+            ol = j < R - 1 ? El[j + 1] : r_ol;
+            nh = j < R - 1 ? En[j + 1] : r_nh;
+            nl = j < R - 1 ? Eln[j + 1] : r_nl;
+          } else {
+            oh = j ? E[j - 1] : l_oh;
+            ol = j ? El[j - 1] : l_ol;
+            nh = j ? En[j - 1] : l_nh;
+            nl = j ? Eln[j - 1] : l_nl;
+          }
+          if ((lft ? a.bc_l : a.bc_r) == 1) {
+            Bh[j] = Bl[j] = real(0);
+          } else {
+            Bh[j] = oh;
+            Bl[j] = ol;
+            fld_axpy_diff<real>(Bh[j], Bl[j], real(lft ? a.kmur_l : a.kmur_r), nh, nl, E[j], El[j], real(0));
+          }
         }
       }
 #pragma unroll
-      for (int j = 0; j < R; ++j) En[j] = Eb[j];
+      for (int j = 0; j < R; ++j) {
+        En[j] = Bh[j];
+        Eln[j] = Bl[j];
+      }
     }
     if (any_probe && pmask) {
 #pragma unroll
@@ -536,12 +678,14 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
         if (pmask & (1u << j))
           for (int p = 0; p < a.n_probe; ++p)
             if (a.pr_cell[p] == g0 + j && a.pr_q[p] < 2)
-              rec[(size_t)p * a.nt + n] = a.pr_q[p] == 0 ? En[j] : Hn[j];
+              rec[(size_t)p * a.nt + n] = a.pr_q[p] == 0 ? fld_val<real>(En[j], Eln[j]) : fld_val<real>(Hn[j], Hln[j]);
     }
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       E[j] = En[j];
+      El[j] = Eln[j];
       H[j] = Hn[j];
+      Hl[j] = Hln[j];
     }
   }
 
@@ -550,11 +694,17 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
   if (!owned) return;
   real *Eo = reinterpret_cast<real *>(a.E[cur ^ 1]);
   real *Ho = reinterpret_cast<real *>(a.H[cur ^ 1]);
+  real *Elo = reinterpret_cast<real *>(a.El[cur ^ 1]);
+  real *Hlo = reinterpret_cast<real *>(a.Hl[cur ^ 1]);
   real *Do = reinterpret_cast<real *>(a.D[cur ^ 1]);
   real *Co = reinterpret_cast<real *>(a.C[cur ^ 1]);
   if (g0 + R <= a.nx) {
     st_row<real, R>(Eo + base, E);
     st_row<real, R>(Ho + base, H);
+    if (FF) {
+      st_row<real, R>(Elo + base, El);
+      st_row<real, R>(Hlo + base, Hl);
+    }
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       st_row<real, R>(Do + (size_t)i * a.ld + base, d[i]);
@@ -566,6 +716,10 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
       if (g0 + j < a.nx) {
         Eo[base + j] = E[j];
         Ho[base + j] = H[j];
+        if (FF) {
+          Elo[base + j] = El[j];
+          Hlo[base + j] = Hl[j];
+        }
 #pragma unroll
         for (int i = 0; i < K; ++i) {
           Do[(size_t)i * a.ld + base + j] = d[i][j];
@@ -576,11 +730,64 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
 }
 
 // ========================================================= state check
+// Number of negative pivots of the LDL^H factorisation of A - sigma I (no
+// pivoting): by Sylvester's law of inertia, the number of eigenvalues of the
+// Hermitian A below sigma.  Pivots within 1e-14 of zero (relative to the
+// scale of A) count as negative, so that no pivot divides by ~0.
+template <int N>
+__device__ __forceinline__ int ldl_neg_count(const double (&re)[N][N], const double (&im)[N][N], double sigma,
+                                             double scale) {
+  double lr[N][N], li[N][N], d[N];
+  int neg = 0;
+  for (int k = 0; k < N; ++k) {
+    double s = re[k][k] - sigma;
+    for (int j = 0; j < k; ++j) s -= (lr[k][j] * lr[k][j] + li[k][j] * li[k][j]) * d[j];
+    if (fabs(s) < 1e-14 * scale) s = -1e-14 * scale;
+    d[k] = s;
+    neg += s < 0.0;
+    for (int i = k + 1; i < N; ++i) {
+      // l_ik = (a_ik - sum_j l_ij conj(l_kj) d_j) / d_k
+      double ar = re[i][k], ai = im[i][k];
+      for (int j = 0; j < k; ++j) {
+        ar -= (lr[i][j] * lr[k][j] + li[i][j] * li[k][j]) * d[j];
+        ai -= (li[i][j] * lr[k][j] - lr[i][j] * li[k][j]) * d[j];
+      }
+      lr[i][k] = ar / s;
+      li[i][k] = ai / s;
+    }
+  }
+  return neg;
+}
+
+// Smallest eigenvalue of the Hermitian matrix re + i im by bisection between
+// the Gershgorin lower bound and the smallest diagonal entry.
+template <int N>
+__device__ double min_eig_bisect(const double (&re)[N][N], const double (&im)[N][N]) {
+  double lo = 1e300, hi = 1e300, scale = 0.0;
+  for (int i = 0; i < N; ++i) {
+    double r = 0.0;
+    for (int j = 0; j < N; ++j)
+      if (j != i) r += hypot(re[i][j], im[i][j]);
+    lo = fmin(lo, re[i][i] - r);
+    hi = fmin(hi, re[i][i]);
+    scale = fmax(scale, fabs(re[i][i]) + r);
+  }
+  if (!(scale > 0.0)) return hi;
+  for (int it = 0; it < 64 && hi - lo > 1e-15 * scale; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (ldl_neg_count<N>(re, im, mid, scale) >= 1)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  return hi;
+}
+
 // For each listed cell, rebuild the stored density matrix x (FP64, true
 // value delta - compensation, reference state zref[slot][N*N] in full real
 // coordinates), and report its trace deviation and smallest eigenvalue
-// (cyclic Jacobi on the Hermitian N x N matrix).  Non-finite values set
-// bit 0 of flags[0].
+// (inertia bisection above).  Non-finite values of the state or of the
+// cell's fields (both ping-pong buffers) set bit 0 of flags[0].
 template <typename real, int N>
 __global__ void k_check(const Args a, int cur, const int *cells, int n_cells, double *min_eig,
                         double *tr_dev, const double *zref) {
@@ -625,45 +832,13 @@ __global__ void k_check(const Args a, int cur, const int *cells, int n_cells, do
       im[i][j] = y[N + 2 * q + 1];
       im[j][i] = -y[N + 2 * q + 1];
     }
-  // cyclic complex Jacobi: rotate away |a_pq| with the phase-removed real rotation
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    double off = 0.0;
-    for (int i = 0; i < N; ++i)
-      for (int j = 0; j < N; ++j)
-        if (i != j) off += re[i][j] * re[i][j] + im[i][j] * im[i][j];
-    if (off < 1e-30) break;
-    for (int p = 0; p < N - 1; ++p)
-      for (int r = p + 1; r < N; ++r) {
-        const double mag = hypot(re[p][r], im[p][r]);
-        if (mag < 1e-300) continue;
-        const double pr = re[p][r] / mag, pi = im[p][r] / mag;   // e^{i phi}
-        const double tau = (re[r][r] - re[p][p]) / (2.0 * mag);
-        const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-        const double c = 1.0 / sqrt(1.0 + tt * tt), s = tt * c;
-        // W: identity except W_pp = c, W_pr = s, W_rp = -s e^{-i phi}, W_rr = c e^{-i phi}
-        // A <- W^+ A W  (columns then rows)
-        for (int i = 0; i < N; ++i) {   // A W : columns p, r
-          const double ap_r = re[i][p], ap_i = im[i][p], ar_r = re[i][r], ar_i = im[i][r];
-          // col p: c a_p - s e^{-i phi} a_r
-          const double er = pr * ar_r + pi * ar_i, ei = pr * ar_i - pi * ar_r;   // e^{-i phi} a_r
-          re[i][p] = c * ap_r - s * er;
-          im[i][p] = c * ap_i - s * ei;
-          re[i][r] = s * ap_r + c * er;
-          im[i][r] = s * ap_i + c * ei;
-        }
-        for (int j = 0; j < N; ++j) {   // W^+ A : rows p, r
-          const double ap_r = re[p][j], ap_i = im[p][j], ar_r = re[r][j], ar_i = im[r][j];
-          const double er = pr * ar_r - pi * ar_i, ei = pr * ar_i + pi * ar_r;   // e^{+i phi} a_r
-          re[p][j] = c * ap_r - s * er;
-          im[p][j] = c * ap_i - s * ei;
-          re[r][j] = s * ap_r + c * er;
-          im[r][j] = s * ap_i + c * ei;
-        }
-        re[p][r] = re[r][p] = im[p][r] = im[r][p] = 0.0;
-      }
+  double mn = min_eig_bisect<N>(re, im);
+  {
+    const real *E = reinterpret_cast<const real *>(a.E[0]), *E1 = reinterpret_cast<const real *>(a.E[1]);
+    const real *H = reinterpret_cast<const real *>(a.H[0]), *H1 = reinterpret_cast<const real *>(a.H[1]);
+    finite &= isfinite((double)E[idx]) && isfinite((double)E1[idx]) && isfinite((double)H[idx]) &&
+              isfinite((double)H1[idx]);
   }
-  double mn = re[0][0];
-  for (int i = 1; i < N; ++i) mn = fmin(mn, re[i][i]);
   if (!finite || !isfinite(mn)) {
     atomicOr(a.flags, 1);
     mn = -1e300;

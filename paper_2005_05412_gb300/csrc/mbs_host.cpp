@@ -388,7 +388,7 @@ struct SrcHost {
 struct Bundle {  // device buffers of one precision
   bool ready = false;
   size_t rb = 8;
-  void *E[2] = {}, *H[2] = {}, *D[2] = {}, *C[2] = {}, *pd = nullptr, *Dinit = nullptr;
+  void *E[2] = {}, *H[2] = {}, *El[2] = {}, *Hl[2] = {}, *D[2] = {}, *C[2] = {}, *pd = nullptr, *Dinit = nullptr;
   void *emc = nullptr, *qpar = nullptr, *pcell = nullptr, *pr_coef = nullptr, *rec = nullptr;
   std::vector<void *> src_tabs;
 };
@@ -606,6 +606,24 @@ int upload(const std::vector<double> &h, void **dptr, int prec) {
   return 0;
 }
 
+// per-step source table: FP64 as is; FP32 as [2][nt] high and low words of
+// each value (v = hi + lo to ~2^-48 relative)
+int upload_src(const std::vector<double> &h, void **dptr, int prec) {
+  if (prec == 0) return upload(h, dptr, 0);
+  const size_t n = h.size();
+  std::vector<float> f(2 * n);
+  for (size_t i = 0; i < n; ++i) {
+    f[i] = (float)h[i];
+    f[n + i] = (float)(h[i] - (double)f[i]);
+  }
+  cudaError_t e = cudaMalloc(dptr, f.size() * sizeof(float));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  if (g_h2d) *g_h2d += (long long)(f.size() * sizeof(float));
+  e = cudaMemcpy(*dptr, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  return 0;
+}
+
 template <typename T>
 int upload_raw(const std::vector<T> &h, T **dptr) {
   if (h.empty()) {
@@ -624,6 +642,8 @@ void free_bundle(Bundle &b) {
   for (int i = 0; i < 2; ++i) {
     cudaFree(b.E[i]);
     cudaFree(b.H[i]);
+    cudaFree(b.El[i]);
+    cudaFree(b.Hl[i]);
     cudaFree(b.D[i]);
     cudaFree(b.C[i]);
   }
@@ -649,6 +669,10 @@ int ensure_bundle(mbs_scenario_s *s, int prec) {
   for (int i = 0; i < 2; ++i) {
     if ((e = cudaMalloc(&b.E[i], row)) != cudaSuccess) return cuda_fail(e, "cudaMalloc E");
     if ((e = cudaMalloc(&b.H[i], row)) != cudaSuccess) return cuda_fail(e, "cudaMalloc H");
+    if (prec == 1) {
+      if ((e = cudaMalloc(&b.El[i], row)) != cudaSuccess) return cuda_fail(e, "cudaMalloc El");
+      if ((e = cudaMalloc(&b.Hl[i], row)) != cudaSuccess) return cuda_fail(e, "cudaMalloc Hl");
+    }
     if ((e = cudaMalloc(&b.D[i], row * std::max(K, 1))) != cudaSuccess) return cuda_fail(e, "cudaMalloc D");
     if ((e = cudaMalloc(&b.C[i], row * std::max(K, 1))) != cudaSuccess) return cuda_fail(e, "cudaMalloc C");
   }
@@ -664,9 +688,9 @@ int ensure_bundle(mbs_scenario_s *s, int prec) {
   if ((e = cudaMemset(b.rec, 0, nrec * rb)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
   for (auto &sr : s->src) {
     void *p = nullptr;
-    if ((rc = upload(sr.sH, &p, prec))) return rc;
+    if ((rc = upload_src(sr.sH, &p, prec))) return rc;
     b.src_tabs.push_back(p);
-    if ((rc = upload(sr.sE, &p, prec))) return rc;
+    if ((rc = upload_src(sr.sE, &p, prec))) return rc;
     b.src_tabs.push_back(p);
   }
   b.ready = true;
@@ -687,6 +711,8 @@ mbs::Args make_args(mbs_scenario_s *s, int prec) {
   for (int i = 0; i < 2; ++i) {
     a.E[i] = b.E[i];
     a.H[i] = b.H[i];
+    a.El[i] = b.El[i];
+    a.Hl[i] = b.Hl[i];
     a.D[i] = b.D[i];
     a.C[i] = b.C[i];
   }
@@ -878,7 +904,7 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
   for (int i = 0; i < n_mat; ++i) {
     const MatDesc &m = dev->mats[i];
     const double eps = kEps0 * m.eps_r, k = dt * m.sigma / (2 * eps);
-    s->emc[i * 4 + 0] = (1 - k) / (1 + k);
+    s->emc[i * 4 + 0] = (1 - k) / (1 + k) - 1.0;   // a' - 1 (exactly 0 without loss)
     s->emc[i * 4 + 1] = (dt / eps) / (1 + k) / (dz * eta0);
     s->emc[i * 4 + 2] = dt * eta0 / (dz * kMu0 * m.mu_r);
   }
@@ -973,6 +999,9 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
     if (sr.kind < 0 || sr.kind > 2) return fail(MBS_E_INVALID, "source %d: bad kind", k);
     if (sr.cell < 2 || sr.cell > nx - 3) return fail(MBS_E_INVALID, "source %d: cell must be in [2, n_cells-3]", k);
     if (!(sr.tau > 0)) return fail(MBS_E_INVALID, "source %d: tau must be > 0", k);
+    if (!std::isfinite(sr.e0) || !std::isfinite(sr.tau) || !std::isfinite(sr.t0) || !std::isfinite(sr.omega) ||
+        !std::isfinite(sr.phase))
+      return fail(MBS_E_INVALID, "source %d: non-finite parameter", k);
     SrcHost h;
     h.kind = sr.kind;
     h.cell = sr.cell;
@@ -1093,6 +1122,8 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     if ((e = cudaMemsetAsync(b.E[i], 0, row, st)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(b.H[i], 0, row, st)) != cudaSuccess) break;
+    if (b.El[i] && (e = cudaMemsetAsync(b.El[i], 0, row, st)) != cudaSuccess) break;
+    if (b.Hl[i] && (e = cudaMemsetAsync(b.Hl[i], 0, row, st)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(b.C[i], 0, row * K, st)) != cudaSuccess) break;
     e = cudaMemcpyAsync(b.D[i], b.Dinit, row * K, cudaMemcpyDeviceToDevice, st);
   }

@@ -1,5 +1,6 @@
 // mbs_internal.h -- private interface between the host setup (mbs_host.cpp)
-// and the CUDA kernels (mbs_kernels.cu) of the Maxwell-Bloch hot path.
+// and the CUDA kernels (mbs_device.cuh, instantiated in mbs_tiled.cu and
+// mbs_plain*.cu) of the Maxwell-Bloch hot path.
 //
 // State representation on the device (per medium cell):
 //   * the density matrix after the first half of the constant propagator,
@@ -16,9 +17,10 @@
 //   u = v - x_ref = delta + (R - 1) x
 //   delta' = A u + c          (A = exp(L0 dt) on deviations, c its offset)
 //   d_t P^{n+1/2} = n3D (g . u + g0)  (tr{mu L0 exp(L0 dt/2) v})
-//   E^{n+1} = a E^n - b' Gamma d_t P + b' (H_{m+1} - H_m)/dz
+//   E^{n+1} = E^n + (a' - 1) E^n - b' Gamma d_t P + b' (H_{m+1} - H_m)/dz
 // Fields: E in V/m; H is stored normalised, H^ = eta0 H (V/m), so that in
-// vacuum at Courant number 1 both field coefficients are exactly 1.
+// vacuum at Courant number 1 both field coefficients are exactly 1.  In FP32
+// each field value is a float-float pair (high + low word).
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -50,8 +52,9 @@ struct SrcDev {
   int face;         // face receiving the H correction (-1: none)
   int cell;         // cell receiving the E correction / hard value
   int pad_;
-  const void *sH;   // [nt] H^ correction per step (added at `face`)
-  const void *sE;   // [nt] E correction (or hard value) per step
+  const void *sH;   // H^ correction per step (added at `face`): FP64 [nt],
+                    // FP32 [2][nt] (high words, then low words)
+  const void *sE;   // E correction (or hard value) per step, same layout
 };
 
 // Everything a launch needs (passed by value).
@@ -61,11 +64,12 @@ struct Args {
   int nx, ld, off;             // cells, padded row length, index of cell 0
   long long nt;                // total steps of the scenario
   void *E[2], *H[2];           // [ld] ping-pong (plain path updates H in place in H[0])
+  void *El[2], *Hl[2];         // FP32: low words of the float-float fields (else null)
   void *D[2], *C[2];           // [K][ld] deviation / Kahan compensation
   void *pd;                    // [ld] coupling term of the plain path
   const uint8_t *mat;          // [ld] material id per cell (pad cells: n_mat)
   int n_mat_all;               // materials incl. the pad material
-  const void *emc;             // [n_mat_all][4]: a, b^, c^, 0
+  const void *emc;             // [n_mat_all][4]: a' - 1, b^, c^, 0
   const int *qslot;            // [n_mat_all]: parameter slot or -1
   const void *qpar;            // [n_slot][qstride]
   int n_slot, qstride;
@@ -82,7 +86,7 @@ struct Args {
   int *flags;                  // [4] device status words
 };
 
-// Launchers (mbs_kernels.cu).  All return 0 or a cudaError_t value.
+// Launchers (mbs_tiled.cu, mbs_plain.cu).  All return 0 or a cudaError_t value.
 int launch_plain_step(const Args &a, long long n, int cur, void *stream);
 int launch_tiled(const Args &a, long long n0, int nsteps, int T, int cur, void *stream);
 int tiled_supported(int prec, int N);

@@ -188,11 +188,13 @@ def test_api_errors_on_gpu():
 
 
 def test_numeric_failure_is_a_status_not_a_fault():
-    """An overflowing source drives the state non-finite; the device state
-    check reports MBS_E_NUMERIC (no GPU fault) and the context stays usable.
-    A non-finite step operator is rejected when the scenario is built."""
+    """Two superposed 1.7e308 V/m pulses overflow the fields to inf and
+    the state to NaN; the device state check reports MBS_E_NUMERIC (no
+    GPU fault) and the context stays usable.  A non-finite step operator is
+    rejected when the scenario is built, non-finite source parameters too."""
     p = W.sit_2lvl(n_cells=64, t_end=0.0, n_steps=200)
-    p.sources[0].e0, p.sources[0].t0 = 1e307, 0.0
+    s = p.sources[0]
+    p.sources = [W.Source(W.SRC_TFSF_RIGHT, c, 1.7e308, s.tau, 0.0, s.omega, 1.0) for c in (3, 5)]
     for prec in ("fp64", "fp32"):
         with pytest.raises(mbs.MBSError) as e:
             mbs.run(p, precision=prec, algo="plain", check_every=50)
@@ -202,5 +204,36 @@ def test_numeric_failure_is_a_status_not_a_fault():
     with pytest.raises(mbs.MBSError) as e:
         mbs.run(q, precision="fp64")
     assert e.value.status == mbs.MBS_E_NUMERIC
+    q = W.sit_2lvl(n_cells=64, t_end=0.0, n_steps=8)
+    q.sources[0].e0 = float("nan")
+    with pytest.raises(mbs.MBSError) as e:
+        mbs.run(q, precision="fp64")
+    assert e.value.status == mbs.MBS_E_INVALID
     ok = mbs.run(sit_small().replace(n_steps=10, t_end=0.0), precision="fp32")
     assert np.all(np.isfinite(ok["records"]))
+
+
+@pytest.mark.parametrize("n_levels", [2, 3, 4, 5, 6])
+def test_state_check_min_eigenvalue(n_levels):
+    """The device state check reports the smallest eigenvalue of the stored
+    density matrix: after one source-free step from rho0 that is
+    exp(1.5 L0 dt) rho0 (the state carries half a step ahead)."""
+    import scipy.linalg as sl
+    p = W.ladder_6lvl(n_cells=64, n_steps=1)
+    q = p.qms[0]
+    n = n_levels
+    rng = np.random.default_rng(n)
+    a = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    rho0 = a @ a.conj().T + 0.05 * np.eye(n)
+    rho0 /= np.trace(rho0).real
+    keep = [k for k, o in enumerate(q.lindblad_ops) if not np.abs(o[n:, :]).any() and not np.abs(o[:, n:]).any()]
+    q2 = W.QM(n, q.density, q.h0[:n, :n], q.mu[:n, :n], rho0, q.lindblad_rates[keep],
+              q.lindblad_ops[keep][:, :n, :n])
+    p = p.replace(qms=[q2], sources=[], probes=[W.Probe(10, W.Q_E)])
+    L0 = oracle.liouvillian(q2)
+    x = (sl.expm(1.5 * L0 * (p.dz / W.C0)) @ rho0.reshape(-1)).reshape(n, n)
+    ref = np.linalg.eigvalsh((x + x.conj().T) / 2).min()
+    for prec, tol in (("fp64", 1e-12), ("fp32", 1e-6)):
+        st = mbs.run(p, precision=prec, algo="plain")["stats"]
+        assert st["min_eig"] == pytest.approx(ref, abs=tol)
+        assert st["max_trace_dev"] <= tol

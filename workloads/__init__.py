@@ -218,6 +218,12 @@ def rule_probes(m_s, n_cells, n_steps, fracs=(0.25, 0.5, 0.75)):
     return [m_s + int(math.floor(f * span)) for f in fracs]
 
 
+def in_medium(cell, n_cells, frac_lo=0.05, frac_hi=0.95):
+    """Whether a cell centre lies in the 5 %-95 % medium region."""
+    x = (cell + 0.5) / n_cells
+    return frac_lo <= x < frac_hi
+
+
 def _medium_device(n_cells, dz, frac_lo=0.05, frac_hi=0.95, qm_index=0):
     length = n_cells * dz
     mats = [Material(), Material(qm=qm_index)]
@@ -248,7 +254,9 @@ def sit_2lvl(n_cells=2048, t_end=1e-12, n_steps=0, pulse_area=2.0 * math.pi,
     nt = n_steps if n_steps > 0 else int(math.ceil(t_end / dt))
     probes = []
     for c in rule_probes(SOURCE_CELL, n_cells, nt, probe_fracs):
-        probes += [Probe(c, Q_E), Probe(c, Q_RHO_RE, 0, 0)]
+        probes.append(Probe(c, Q_E))
+        if in_medium(c, n_cells):
+            probes.append(Probe(c, Q_RHO_RE, 0, 0))
     return Problem("sit_2lvl", [qm], mats, regs, length, n_cells, t_end=t_end,
                    n_steps=n_steps, sources=[src], probes=probes)
 
@@ -295,7 +303,8 @@ def lambda_3lvl(n_cells=262_144, n_steps=100_000, tau=100e-15, t0=600e-15,
     probes = []
     for c in rule_probes(SOURCE_CELL, n_cells, n_steps):
         probes.append(Probe(c, Q_E))
-        probes += [Probe(c, Q_RHO_RE, k, k) for k in range(n)]
+        if in_medium(c, n_cells):
+            probes += [Probe(c, Q_RHO_RE, k, k) for k in range(n)]
     return Problem("lambda_3lvl", [qm], mats, regs, length, n_cells, n_steps=n_steps,
                    sources=srcs, probes=probes)
 
@@ -329,7 +338,8 @@ def ladder_6lvl(n_cells=131_072, n_steps=50_000, seed=3, tau=10e-15, t0=60e-15,
     probes = []
     for c in rule_probes(SOURCE_CELL, n_cells, n_steps):
         probes.append(Probe(c, Q_E))
-        probes += [Probe(c, Q_RHO_RE, k, k) for k in range(n)]
+        if in_medium(c, n_cells):
+            probes += [Probe(c, Q_RHO_RE, k, k) for k in range(n)]
     return Problem("ladder_6lvl", [qm], mats, regs, length, n_cells, n_steps=n_steps,
                    sources=[src], probes=probes)
 
