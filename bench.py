@@ -274,12 +274,16 @@ def e2e(p, mbs, args, torch, stream, reps=2):
 
 def load_traffic(args):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, when it was taken on the current kernel (else null)."""
+    summary (profiles/traffic.json), or None when the kernel source changed
+    after the capture (the file records a hash of the source it measured)."""
+    import hashlib
     f = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(f))
-        key = f"{args.precision}_T{args.tile}"
-        return d.get(key)
+        src = open(os.path.join(ROOT, d["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != d["kernel_source_sha256_16"]:
+            return None
+        return d.get(f"{args.precision}_T{args.tile}")
     except Exception:
         return None
 
