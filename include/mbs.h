@@ -210,6 +210,34 @@ int mbs_device_propagators(mbs_device_t dev, int qm, double dt,
 int mbs_scenario_counters(mbs_scenario_t s, long long *h2d_bytes, long long *d2h_bytes,
                           long long *kernel_launches);
 
+/* Largest number of density matrices mbs_check_rho_static accepts per call. */
+#define MBS_STATIC_CHECK_MAX 65536
+
+/* Density-matrix check that allocates no device memory.  It has no
+ * counterpart in the paper: it exists for callers that cannot call
+ * cudaMalloc -- code that runs while a CUDA graph is being captured, or
+ * inside a framework that owns every device allocation -- and still want the
+ * positivity/trace check that mbs_solve applies to its own state.
+ *   rho       device pointer, n matrices of n_levels x n_levels complex
+ *             (interleaved re, im, row-major), read only
+ *   n         1 .. MBS_STATIC_CHECK_MAX (larger n: MBS_E_INVALID, no work)
+ *   n_levels  2 .. 6
+ *   out       device pointer to 3 doubles, written: smallest eigenvalue of
+ *             the Hermitian parts of the finite matrices, largest
+ *             |tr rho - 1|, number of matrices with non-finite entries
+ *   cuda_stream  cudaStream_t or NULL; the call only enqueues work on it
+ *             (asynchronous with respect to the host).
+ * Scratch: a fixed static device array of 3 doubles per matrix for
+ * MBS_STATIC_CHECK_MAX matrices (about 1.5 MB), held by every GPU that loads
+ * the library until the process exits.  No cudaMalloc, cudaFree or other
+ * allocating call is made.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call shares the array and it
+ * keeps the last call's contents; each call overwrites the entries it reads,
+ * so nothing needs clearing, but calls that overlap on the GPU (on different
+ * streams, or from several host threads) race on it. */
+int mbs_check_rho_static(const double *rho, int n, int n_levels, double *out, void *cuda_stream);
+
 void mbs_scenario_destroy(mbs_scenario_t s);
 void mbs_device_destroy(mbs_device_t d);
 

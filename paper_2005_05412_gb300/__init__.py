@@ -75,7 +75,7 @@ _lib = None
 # every symbol include/mbs.h declares
 EXPORTS = ["mbs_device_create", "mbs_device_destroy", "mbs_device_propagators", "mbs_scenario",
            "mbs_scenario_destroy", "mbs_scenario_info", "mbs_scenario_stats", "mbs_scenario_counters", "mbs_solve",
-           "mbs_fetch_records", "mbs_last_error", "mbs_abi_version"]
+           "mbs_fetch_records", "mbs_last_error", "mbs_abi_version", "mbs_check_rho_static"]
 
 
 def lib():
@@ -102,6 +102,8 @@ def lib():
         L.mbs_last_error.restype = C.c_char_p
         L.mbs_last_error.argtypes = []
         L.mbs_abi_version.restype = i
+        L.mbs_check_rho_static.argtypes = [vp, i, i, vp, vp]
+        L.mbs_check_rho_static.restype = i
         for f in ["mbs_device_create", "mbs_device_propagators", "mbs_scenario", "mbs_scenario_info", "mbs_scenario_counters",
                   "mbs_scenario_stats", "mbs_solve", "mbs_fetch_records"]:
             getattr(L, f).restype = i
@@ -252,6 +254,19 @@ def mbs_device_propagators(device: Device, qm: int, dt: float, n_levels: int):
                                         ("lam", "V", "A", "Ah", "c", "zref", "g", "g0")]))
     out["g0"] = float(out["g0"][0])
     return out
+
+
+MBS_STATIC_CHECK_MAX = 65536
+
+
+def mbs_check_rho_static(rho_ptr: int, n: int, n_levels: int, out_ptr: int, stream=None) -> int:
+    """Allocation-free density-matrix check (see include/mbs.h).  rho_ptr:
+    device address of n complex128 n_levels x n_levels matrices; out_ptr:
+    device address of 3 float64 (min eigenvalue, max |tr - 1|, non-finite
+    count).  Enqueues on `stream` (a cudaStream_t handle or None)."""
+    return _check(lib().mbs_check_rho_static(C.c_void_p(int(rho_ptr)), int(n), int(n_levels),
+                                             C.c_void_p(int(out_ptr)),
+                                             None if stream is None else C.c_void_p(int(stream))))
 
 
 def mbs_abi_version() -> int:

@@ -763,6 +763,8 @@ double light_speed(const MatDesc &m) { return 1.0 / std::sqrt(kEps0 * m.eps_r * 
 
 }  // namespace
 
+int mbs::set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
 // ============================================================ C ABI
 extern "C" {
 

@@ -86,6 +86,10 @@ struct Args {
   int *flags;                  // [4] device status words
 };
 
+// Records `msg` as the calling thread's last error (mbs_last_error) and
+// returns `code` (mbs_host.cpp).
+int set_error(int code, const char *msg);
+
 // Launchers (mbs_tiled.cu, mbs_plain.cu).  All return 0 or a cudaError_t value.
 int launch_plain_step(const Args &a, long long n, int cur, void *stream);
 int launch_tiled(const Args &a, long long n0, int nsteps, int T, int cur, void *stream);
