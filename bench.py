@@ -322,7 +322,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sit_2lvl_jitter")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--tile", type=int, default=12)
     ap.add_argument("--quick", action="store_true", help="skip the FP64, e2e and CPU legs")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--nsteps", type=int, default=0, help="override the workload's step count (profiling)")

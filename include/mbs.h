@@ -159,7 +159,7 @@ enum { MBS_ALGO_AUTO = 0,
 typedef struct {
     int precision;     /* MBS_PREC_* */
     int algo;          /* MBS_ALGO_* */
-    int tile_steps;    /* steps per tiled launch (multiple of 4), 0 = default */
+    int tile_steps;    /* steps per tiled launch (multiple of 4), 0 = default (12) */
     int check_every;   /* steps between device-side state checks, 0 = only at the end */
 } mbs_opts;
 

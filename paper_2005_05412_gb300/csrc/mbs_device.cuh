@@ -140,6 +140,24 @@ struct PrmReg {
   __device__ __forceinline__ real zr(int i) const { return mb[K * K + 2 * K + 1 + P + i]; }
 };
 
+// Two-level media whose step operator has the optical-Bloch pattern (the
+// host verifies it): A - I has non-zeros only at (0,0), (0,2), (1,1),
+// (2,0), (2,2), the affine offset vanishes and the coupling has no (1)
+// component.  Per cell: 7 rows of the per-cell table instead of 16.
+template <typename real>
+struct PrmBloch2 {
+  static constexpr int K = 3, P = 1;
+  real a00, a02, a11, a20, a22, w0c, w2c;
+  const real *mb;
+  __device__ __forceinline__ real kap(int q) const { return mb[K * K + 2 * K + 1 + q]; }
+  __device__ __forceinline__ real zr(int i) const { return mb[K * K + 2 * K + 1 + P + i]; }
+};
+
+template <typename real, int N, bool KAHAN, class Prm>
+__device__ __forceinline__ void bloch_accumulate(const Prm &q, const real (&u)[N * N - 1],
+                                                 const real (&rx)[N * (N - 1)], real (&d)[N * N - 1],
+                                                 real (&cc)[N * N - 1]);
+
 // ------------------------------------------------- one cell's Bloch step
 // delta^n -> delta^{n+1}; returns the coupling w . u + w0 and leaves the
 // rotated deviation u (= v - x_ref) in `u`.
@@ -167,6 +185,16 @@ __device__ __forceinline__ real bloch_step(const Prm &q, real e, real (&d)[N * N
   real pw = q.w0();
 #pragma unroll
   for (int i = 0; i < K; ++i) pw += q.w(i) * u[i];
+  bloch_accumulate<real, N, KAHAN>(q, u, rx, d, cc);
+  return pw;
+}
+
+// delta += c + [0 | (R - 1) x] + (A - I) u   (compensated in FP32)
+template <typename real, int N, bool KAHAN, class Prm>
+__device__ __forceinline__ void bloch_accumulate(const Prm &q, const real (&u)[N * N - 1],
+                                                 const real (&rx)[N * (N - 1)], real (&d)[N * N - 1],
+                                                 real (&cc)[N * N - 1]) {
+  constexpr int K = N * N - 1, NP = N - 1;
   if constexpr (K <= 15) {
 #pragma unroll
     for (int i = 0; i < K; ++i) {
@@ -192,6 +220,35 @@ __device__ __forceinline__ real bloch_step(const Prm &q, real e, real (&d)[N * N
       else
         d[i] += acc;
     }
+  }
+}
+
+// structured two-level step (same arithmetic as bloch_step restricted to the
+// optical-Bloch pattern)
+template <typename real, bool KAHAN>
+__device__ __forceinline__ real bloch_step_b2(const PrmBloch2<real> &q, real e, real (&d)[3], real (&cc)[3],
+                                              real (&u)[3]) {
+  real s, cm1;
+  sincos_m1(q.kap(0) * e, s, cm1);
+  const real xa = q.zr(0) + d[1];
+  const real xb = q.zr(1) + d[2];
+  const real ra = cm1 * xa - s * xb;
+  const real rb = s * xa + cm1 * xb;
+  u[0] = d[0];
+  u[1] = d[1] + ra;
+  u[2] = d[2] + rb;
+  const real pw = q.w0c * u[0] + q.w2c * u[2];
+  const real a0 = q.a00 * u[0] + q.a02 * u[2];
+  const real a1 = ra + q.a11 * u[1];
+  const real a2 = rb + q.a20 * u[0] + q.a22 * u[2];
+  if (KAHAN) {
+    kahan_add(d[0], cc[0], a0);
+    kahan_add(d[1], cc[1], a1);
+    kahan_add(d[2], cc[2], a2);
+  } else {
+    d[0] += a0;
+    d[1] += a1;
+    d[2] += a2;
   }
   return pw;
 }
@@ -242,6 +299,19 @@ __device__ __forceinline__ void fld_axpy_diff(real &fh, real &fl, real c, real x
     const float dl = de + (xrl - xll);
     two_prod(c, dh, ph, pe);
     ff_add(fh, fl, ph, pe + c * dl + extra);
+  }
+}
+
+// f += (xr - xl) + extra: the unit-coefficient case (vacuum-like media at
+// Courant number 1, where the FP32 coefficients round to exactly 1 and 0)
+template <typename real>
+__device__ __forceinline__ void fld_add_diff(real &fh, real &fl, real xrh, real xrl, real xlh, real xll, real extra) {
+  if constexpr (sizeof(real) == 8) {
+    fh += (xrh - xlh) + extra;
+  } else {
+    float dh, de;
+    two_sum(xrh, -xlh, dh, de);
+    ff_add(fh, fl, dh, de + (xrl - xll) + extra);
   }
 }
 
@@ -452,12 +522,18 @@ __device__ __forceinline__ void st_row<double, 4>(double *p, const double (&v)[4
 
 // Warp w owns cells [w*own, (w+1)*own), own = 32 R - 2 T; lane l holds cells
 // tb + l R .. tb + l R + R - 1 with tb = w*own - T.  Reads buffers `cur`,
-// writes the owned cells of buffers cur ^ 1.  PERCELL: per-cell propagator
-// rows are loaded into registers (jittered media).
-template <typename real, int N, int R, bool KAHAN, bool PERCELL>
+// writes the owned cells of buffers cur ^ 1.
+//   PM = 0: step operator of the lane's medium from shared memory;
+//   PM = 1: dense per-cell step operator rows in registers (jittered media);
+//   PM = 2: structured two-level per-cell rows in registers (see PrmBloch2).
+//   UNIT: all field coefficients are exactly 1 (and a' - 1 = 0); cells
+//         outside the grid are then held at zero explicitly.
+template <typename real, int N, int R, bool KAHAN, int PM, bool UNIT>
 __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int nsteps, int T, int cur) {
   constexpr int K = N * N - 1;
   constexpr bool FF = sizeof(real) == 4;
+  constexpr bool PERCELL = PM == 1;
+  static_assert(PM != 2 || N == 2, "structured rows are two-level");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real *s_emc = reinterpret_cast<real *>(smem_raw);
   real *s_q = s_emc + a.n_mat_all * 4;
@@ -470,8 +546,14 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int own = 32 * R - 2 * T;
-  const int c_own = warp * own;
+  int c_own = warp * own;
   if (c_own >= a.nx) return;   // whole warp leaves together
+  // The absorbing right end reads its neighbour's new E (first-order Mur), a
+  // dependency one cell beyond the stencil's light cone: that neighbour must
+  // be owned by the same warp.  If the last cell would start a warp's owned
+  // range, that warp starts 4 cells earlier; the 4 shared cells are valid in
+  // both warps and both write identical values.
+  if (warp > 0 && c_own == a.nx - 1) c_own -= 4;
   const int tb = c_own - T;
   const int g0 = tb + lane * R;         // first cell of this lane
   const int base = a.off + g0;          // its array index (>= 0, multiple of R)
@@ -530,6 +612,26 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
     }
   }
 
+  PrmBloch2<real> b2[PM == 2 ? R : 1];
+  if constexpr (PM == 2) {
+    const real *pc = reinterpret_cast<const real *>(a.pcell2);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      b2[j].mb = mb;
+      b2[j].a00 = pc[(size_t)0 * a.ld + base + j];
+      b2[j].a02 = pc[(size_t)1 * a.ld + base + j];
+      b2[j].a11 = pc[(size_t)2 * a.ld + base + j];
+      b2[j].a20 = pc[(size_t)3 * a.ld + base + j];
+      b2[j].a22 = pc[(size_t)4 * a.ld + base + j];
+      b2[j].w0c = pc[(size_t)5 * a.ld + base + j];
+      b2[j].w2c = pc[(size_t)6 * a.ld + base + j];
+    }
+  }
+  unsigned inside = 0;   // cells of the grid (UNIT mode keeps the others at zero)
+#pragma unroll
+  for (int j = 0; j < R; ++j)
+    if (g0 + j >= 0 && g0 + j < a.nx) inside |= 1u << j;
+
   // warp-uniform: does the tile touch a source, a boundary cell, a probe?
   const int t_lo = tb, t_hi = tb + 32 * R;   // [t_lo, t_hi)
   bool any_src = false;
@@ -558,7 +660,12 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
     for (int j = 0; j < R; ++j) {
       Hn[j] = H[j];
       Hln[j] = Hl[j];
-      fld_axpy_diff<real>(Hn[j], Hln[j], ch[j], E[j], El[j], j ? E[j - 1] : elh, j ? El[j - 1] : ell, real(0));
+      if constexpr (UNIT) {
+        if ((inside & (1u << j)) && g0 + j != 0)   // face 0 is a fixed boundary slot
+          fld_add_diff<real>(Hn[j], Hln[j], E[j], El[j], j ? E[j - 1] : elh, j ? El[j - 1] : ell, real(0));
+      } else {
+        fld_axpy_diff<real>(Hn[j], Hln[j], ch[j], E[j], El[j], j ? E[j - 1] : elh, j ? El[j - 1] : ell, real(0));
+      }
     }
     if (any_src) {
       for (int s = 0; s < a.n_src; ++s) {
@@ -585,7 +692,9 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
           cj[i] = cc[i][j];
         }
         const real ej = fld_val<real>(E[j], El[j]);
-        if (PERCELL)
+        if constexpr (PM == 2)
+          pw[j] = bloch_step_b2<real, KAHAN>(b2[j], ej, dj, cj, u);
+        else if constexpr (PM == 1)
           pw[j] = bloch_step<real, N, KAHAN>(pr[PERCELL ? j : 0], ej, dj, cj, u);
         else
           pw[j] = bloch_step<real, N, KAHAN>(PrmBlock<real, N>{mb}, ej, dj, cj, u);
@@ -609,8 +718,14 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
     for (int j = 0; j < R; ++j) {
       En[j] = E[j];
       Eln[j] = El[j];
-      fld_axpy_diff<real>(En[j], Eln[j], cb[j], j < R - 1 ? Hn[j + 1] : hrh, j < R - 1 ? Hln[j + 1] : hrl, Hn[j],
-                          Hln[j], ca[j] * E[j] - pw[j]);
+      if constexpr (UNIT) {
+        if (inside & (1u << j))
+          fld_add_diff<real>(En[j], Eln[j], j < R - 1 ? Hn[j + 1] : hrh, j < R - 1 ? Hln[j + 1] : hrl, Hn[j], Hln[j],
+                             -pw[j]);
+      } else {
+        fld_axpy_diff<real>(En[j], Eln[j], cb[j], j < R - 1 ? Hn[j + 1] : hrh, j < R - 1 ? Hln[j + 1] : hrl, Hn[j],
+                            Hln[j], ca[j] * E[j] - pw[j]);
+      }
     }
     if (any_src) {
       for (int s = 0; s < a.n_src; ++s) {
@@ -855,14 +970,14 @@ int plain_step_impl(const Args &a, long long n, int cur, cudaStream_t st) {
   return (int)cudaGetLastError();
 }
 
-template <typename real, int N, int R, bool KAHAN, bool PERCELL>
+template <typename real, int N, int R, bool KAHAN, int PM, bool UNIT>
 int tiled_impl(const Args &a, long long n0, int nsteps, int T, int cur, cudaStream_t st) {
   const int own = 32 * R - 2 * T;
   const int n_warps = (a.nx + own - 1) / own;
   const int bs = 128, wpb = bs / 32;
   const int gs = (n_warps + wpb - 1) / wpb;
   const size_t sm = sizeof(real) * (a.n_mat_all * 4 + a.n_slot * a.qstride) + sizeof(int) * a.n_mat_all + 16;
-  k_tiled<real, N, R, KAHAN, PERCELL><<<gs, bs, sm, st>>>(a, n0, nsteps, T, cur);
+  k_tiled<real, N, R, KAHAN, PM, UNIT><<<gs, bs, sm, st>>>(a, n0, nsteps, T, cur);
   return (int)cudaGetLastError();
 }
 

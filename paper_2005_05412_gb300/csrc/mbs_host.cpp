@@ -389,7 +389,7 @@ struct Bundle {  // device buffers of one precision
   bool ready = false;
   size_t rb = 8;
   void *E[2] = {}, *H[2] = {}, *El[2] = {}, *Hl[2] = {}, *D[2] = {}, *C[2] = {}, *pd = nullptr, *Dinit = nullptr;
-  void *emc = nullptr, *qpar = nullptr, *pcell = nullptr, *pr_coef = nullptr, *rec = nullptr;
+  void *emc = nullptr, *qpar = nullptr, *pcell = nullptr, *pcell2 = nullptr, *pr_coef = nullptr, *rec = nullptr;
   std::vector<void *> src_tabs;
 };
 
@@ -401,7 +401,9 @@ struct mbs_scenario_s {
   int ld = 0, off = mbs::PAD;
   int n_slot = 0, qstride = 0;
   // FP64 master copies
-  std::vector<double> emc, qpar, pcell, Dinit, pr_coef, zref;
+  std::vector<double> emc, qpar, pcell, pcell2, Dinit, pr_coef, zref;
+  bool has_b2 = false;   // structured two-level rows available (pcell2)
+  bool unit32 = false;   // every field coefficient rounds to exactly 1 (a' - 1 to 0) in FP32
   std::vector<int> qslot, pr_cell, pr_q;
   std::vector<SrcHost> src;
   double kmur_l = 0, kmur_r = 0;
@@ -652,6 +654,7 @@ void free_bundle(Bundle &b) {
   cudaFree(b.emc);
   cudaFree(b.qpar);
   cudaFree(b.pcell);
+  cudaFree(b.pcell2);
   cudaFree(b.pr_coef);
   cudaFree(b.rec);
   for (void *p : b.src_tabs) cudaFree(p);
@@ -682,6 +685,7 @@ int ensure_bundle(mbs_scenario_s *s, int prec) {
   if ((rc = upload(s->emc, &b.emc, prec))) return rc;
   if ((rc = upload(s->qpar, &b.qpar, prec))) return rc;
   if (s->has_pcell && (rc = upload(s->pcell, &b.pcell, prec))) return rc;
+  if (s->has_b2 && (rc = upload(s->pcell2, &b.pcell2, prec))) return rc;
   if ((rc = upload(s->pr_coef, &b.pr_coef, prec))) return rc;
   const size_t nrec = std::max<size_t>(1, s->pr_cell.size()) * (size_t)s->nt;
   if ((e = cudaMalloc(&b.rec, nrec * rb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc records");
@@ -725,6 +729,8 @@ mbs::Args make_args(mbs_scenario_s *s, int prec) {
   a.n_slot = s->n_slot;
   a.qstride = s->qstride;
   a.pcell = s->has_pcell ? b.pcell : nullptr;
+  a.pcell2 = s->has_b2 ? b.pcell2 : nullptr;
+  a.unit = (prec == 1 && s->unit32) ? 1 : 0;
   a.n_src = (int)s->src.size();
   for (size_t k = 0; k < s->src.size(); ++k) {
     a.src[k].kind = s->src[k].kind;
@@ -995,6 +1001,56 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
   }
   if (bad) return fail(MBS_E_NUMERIC, "non-finite per-cell propagator");
 
+  // structured two-level rows: every medium cell's step operator has the
+  // optical-Bloch pattern (A - I non-zero only at (0,0), (0,2), (1,1), (2,0),
+  // (2,2); no affine offset; no coupling through component 1)
+  if (N == 2 && s->n_slot > 0) {
+    const int stride = s->qstride;
+    auto val = [&](int m, int slot, int r) {   // dense row r of cell m
+      return s->has_pcell ? s->pcell[(size_t)r * ld + off + m] : s->qpar[(size_t)slot * stride + r];
+    };
+    s->pcell2.assign((size_t)7 * ld, 0.0);
+    int bad2 = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad2)
+    for (int m = 0; m < nx; ++m) {
+      const int sl = s->qslot[dev->cell_mat[m]];
+      if (sl < 0) continue;
+      double A[9], c[3], w[3];
+      for (int r = 0; r < 9; ++r) A[r] = val(m, sl, r);
+      for (int r = 0; r < 3; ++r) {
+        c[r] = val(m, sl, 9 + r);
+        w[r] = val(m, sl, 12 + r);
+      }
+      const double w0 = val(m, sl, 15);
+      double amax = 0, wmax = 0;
+      for (double x : A) amax = std::max(amax, std::fabs(x));
+      for (double x : w) wmax = std::max(wmax, std::fabs(x));
+      const double ta = 1e-13 * amax, tw = 1e-13 * wmax;
+      if (std::fabs(A[1]) > ta || std::fabs(A[3]) > ta || std::fabs(A[5]) > ta || std::fabs(A[7]) > ta ||
+          std::fabs(c[0]) > 1e-13 || std::fabs(c[1]) > 1e-13 || std::fabs(c[2]) > 1e-13 || std::fabs(w[1]) > tw ||
+          std::fabs(w0) > tw) {
+        ++bad2;
+        continue;
+      }
+      const size_t col = (size_t)off + m;
+      const double rows[7] = {A[0], A[2], A[4], A[6], A[8], w[0], w[2]};
+      for (int r = 0; r < 7; ++r) s->pcell2[(size_t)r * ld + col] = rows[r];
+    }
+    s->has_b2 = bad2 == 0;
+    if (!s->has_b2) s->pcell2.clear();
+  }
+  // unit field coefficients in FP32
+  {
+    bool unit = true;
+    std::vector<char> used(n_mat, 0);
+    for (int m = 0; m < nx; ++m) used[dev->cell_mat[m]] = 1;
+    for (int i = 0; i < n_mat; ++i)
+      if (used[i])
+        unit = unit && (float)s->emc[i * 4 + 0] == 0.0f && (float)s->emc[i * 4 + 1] == 1.0f &&
+               (float)s->emc[i * 4 + 2] == 1.0f;
+    s->unit32 = unit;
+  }
+
   // sources
   for (int k = 0; k < n_src; ++k) {
     const mbs_source &sr = src[k];
@@ -1136,7 +1192,7 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
 
   int algo = o.algo;
   if (algo == MBS_ALGO_AUTO) algo = mbs::tiled_supported(prec, s->N) && (!s->has_pcell || s->N == 2) ? MBS_ALGO_TILED : MBS_ALGO_PLAIN;
-  int T = o.tile_steps > 0 ? o.tile_steps : 16;
+  int T = o.tile_steps > 0 ? o.tile_steps : 12;
   const int chk = o.check_every > 0 ? o.check_every : 0;
   const int nchk = (int)s->chk_cells.size();
   int cur = 0;

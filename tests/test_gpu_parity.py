@@ -128,6 +128,24 @@ def test_tiled_matches_plain_fp64():
         np.testing.assert_allclose(b, a, rtol=0, atol=1e-13 * np.abs(a).max())
 
 
+@pytest.mark.parametrize("n_levels,tile", [(2, 4), (2, 12), (2, 28), (3, 4), (3, 12)])
+def test_tiled_right_boundary_at_tile_edge(n_levels, tile):
+    """Grids whose last cell would start a warp's owned range; below Courant
+    number 1 the absorbing end reads its neighbour's new field, so the tiled
+    form must keep that neighbour in the same warp."""
+    r = 4 if n_levels == 2 else 2
+    own = 32 * r - 2 * tile
+    nx = 25 * own + 1
+    if n_levels == 2:
+        p = W.sit_2lvl(n_cells=nx, n_steps=1500, courant=W.COURANT_LONG)
+    else:
+        p = W.lambda_3lvl(n_cells=nx, n_steps=1500, tau=20e-15, t0=120e-15)
+    p.probes = p.probes + [W.Probe(nx - 1, W.Q_E), W.Probe(nx - 2, W.Q_E), W.Probe(nx - 1, W.Q_H)]
+    a = mbs.run(p, precision="fp64", algo="plain")["records"]
+    b = mbs.run(p, precision="fp64", algo="tiled", tile_steps=tile)["records"]
+    np.testing.assert_allclose(b, a, rtol=0, atol=1e-13 * np.abs(a).max())
+
+
 # ------------------------------------------------------------ edge cases
 def _edge_problem():
     """Ragged grid, mirrors on both ends, a hard source, a left-going source,
@@ -231,7 +249,7 @@ def test_state_check_min_eigenvalue(n_levels):
               q.lindblad_ops[keep][:, :n, :n])
     p = p.replace(qms=[q2], sources=[], probes=[W.Probe(10, W.Q_E)])
     L0 = oracle.liouvillian(q2)
-    x = (sl.expm(1.5 * L0 * (p.dz / W.C0)) @ rho0.reshape(-1)).reshape(n, n)
+    x = (sl.expm(1.5 * L0 * (p.courant * p.dz / W.C0)) @ rho0.reshape(-1)).reshape(n, n)
     ref = np.linalg.eigvalsh((x + x.conj().T) / 2).min()
     for prec, tol in (("fp64", 1e-12), ("fp32", 1e-6)):
         st = mbs.run(p, precision=prec, algo="plain")["stats"]

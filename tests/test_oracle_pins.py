@@ -461,3 +461,22 @@ def test_golden_sit_listing_pulse_area():
     field = g["sech_amplitude"] / np.cosh((t - t0) / tau) * np.sin(2 * math.pi * g["sech_frequency_hz"] * t)
     traj = oracle.cell_evolve(qm, DT, field)
     assert traj[:, 1, 1].real.max() > 0.8
+
+
+def test_courant_one_is_unstable_in_a_dense_medium():
+    """At Courant number exactly 1 the discrete scheme has no stability
+    margin: the resonant medium makes chi < 0 at the grid's Nyquist
+    frequency, so round-off-level disturbances grow by ~e^(1.5e-3) per step.
+    Slightly below 1 they stay at the physical level.  (This is why the long
+    workloads run at Courant number 1 - 2^-13.)"""
+    out = {}
+    for c in (1.0, W.COURANT_LONG):
+        p = W.sit_2lvl_jitter(n_cells=2048, n_steps=14000, courant=c)
+        psi = np.array([np.cos(1e-6), np.sin(1e-6)])
+        p.qms[0].rho_init = np.outer(psi, psi).astype(complex)
+        p = p.replace(sources=[], probes=[W.Probe(1024, W.Q_E)])
+        e = np.abs(oracle.run(p)["records"][0])
+        out[c] = (e[2000:4000].max(), e[-2000:].max())
+    grow_1, grow_s = (b / a for a, b in out.values())
+    assert grow_1 > 100.0
+    assert grow_s < 10.0

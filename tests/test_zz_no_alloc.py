@@ -39,7 +39,7 @@ def _one_step_problem(n):
     q2 = W.QM(n, q.density, q.h0[:n, :n], q.mu[:n, :n], rho0, q.lindblad_rates[keep],
               q.lindblad_ops[keep][:, :n, :n])
     p = p.replace(qms=[q2], sources=[], probes=[W.Probe(10, W.Q_E)])
-    x = (sl.expm(1.5 * oracle.liouvillian(q2) * (p.dz / W.C0)) @ rho0.reshape(-1)).reshape(n, n)
+    x = (sl.expm(1.5 * oracle.liouvillian(q2) * (p.courant * p.dz / W.C0)) @ rho0.reshape(-1)).reshape(n, n)
     return p, x
 
 

@@ -235,6 +235,16 @@ def _medium_device(n_cells, dz, frac_lo=0.05, frac_hi=0.95, qm_index=0):
 
 DZ_SIT = 150e-6 / 2048          # 73.24 nm cells of the SIT example
 SOURCE_CELL = 2                 # first total-field cell of a left-edge source
+# Courant number of the long runs.  At exactly 1 the Yee scheme has no
+# stability margin, and a dense resonant medium (chi < 0 at the grid's
+# Nyquist frequency) pushes the effective Courant number above 1: round-off
+# then grows by ~e^(1.5e-3) per step and swamps the solution after ~4e4
+# steps.  1 - 2^-13 restores a margin far larger than |chi| there (~3e-7),
+# and is exact in binary32, so that FP32 field coefficients (which then
+# equal it to double rounding) carry no systematic error: a relative
+# coefficient error d shifts the grid's wave speed by d and the phase by
+# 2 pi (L / lambda) d over a path L.
+COURANT_LONG = 1.0 - 2.0 ** -13
 
 
 # ---------------------------------------------------------------------------
@@ -242,7 +252,7 @@ SOURCE_CELL = 2                 # first total-field cell of a left-edge source
 # ---------------------------------------------------------------------------
 def sit_2lvl(n_cells=2048, t_end=1e-12, n_steps=0, pulse_area=2.0 * math.pi,
              gamma1=1e9, gamma2=1e9, density=1e24, omega0=2e14, dipole=1e-29,
-             tau=10e-15, t0=60e-15, probe_fracs=(0.25, 0.5, 0.75)) -> Problem:
+             tau=10e-15, t0=60e-15, probe_fracs=(0.25, 0.5, 0.75), courant=1.0) -> Problem:
     """Two-level SIT medium (paper Sec. 4.1 setup): 5 %-95 % medium,
     eps_r = 1, w0 = -1, rho(0) = diag(1, 0), one-way sech pulse from the left,
     absorbing ends, E and rho_11 recorded at three probes every step."""
@@ -250,7 +260,7 @@ def sit_2lvl(n_cells=2048, t_end=1e-12, n_steps=0, pulse_area=2.0 * math.pi,
     length, mats, regs = _medium_device(n_cells, DZ_SIT)
     e0 = sech_area_amplitude(pulse_area, dipole, tau)
     src = Source(SRC_TFSF_RIGHT, SOURCE_CELL, e0, tau, t0, omega0, 0.0)
-    dt = 1.0 * DZ_SIT / C0
+    dt = courant * DZ_SIT / C0
     nt = n_steps if n_steps > 0 else int(math.ceil(t_end / dt))
     probes = []
     for c in rule_probes(SOURCE_CELL, n_cells, nt, probe_fracs):
@@ -258,7 +268,7 @@ def sit_2lvl(n_cells=2048, t_end=1e-12, n_steps=0, pulse_area=2.0 * math.pi,
         if in_medium(c, n_cells):
             probes.append(Probe(c, Q_RHO_RE, 0, 0))
     return Problem("sit_2lvl", [qm], mats, regs, length, n_cells, t_end=t_end,
-                   n_steps=n_steps, sources=[src], probes=probes)
+                   n_steps=n_steps, sources=[src], probes=probes, courant=courant)
 
 
 def cell_jitter(n_cells, seed=1, spread=0.01) -> np.ndarray:
@@ -268,16 +278,17 @@ def cell_jitter(n_cells, seed=1, spread=0.01) -> np.ndarray:
     return 1.0 + spread * (2.0 * u - 1.0)
 
 
-def sit_2lvl_jitter(n_cells=1_048_576, n_steps=200_000, seed=1, **kw) -> Problem:
+def sit_2lvl_jitter(n_cells=1_048_576, n_steps=200_000, seed=1, courant=COURANT_LONG, **kw) -> Problem:
     """The SIT physics at scale with +-1 % seeded per-cell jitter of the
-    density and of the transition frequency (H0)."""
-    p = sit_2lvl(n_cells=n_cells, n_steps=n_steps, t_end=0.0, **kw)
+    density and of the transition frequency (H0), at the long-run Courant
+    number."""
+    p = sit_2lvl(n_cells=n_cells, n_steps=n_steps, t_end=0.0, courant=courant, **kw)
     return p.replace(name="sit_2lvl_jitter", jitter=cell_jitter(n_cells, seed))
 
 
 def lambda_3lvl(n_cells=262_144, n_steps=100_000, tau=100e-15, t0=600e-15,
                 t1=10e-12, t2=1e-12, probe_area=0.2 * math.pi,
-                control_area=math.pi) -> Problem:
+                control_area=math.pi, courant=COURANT_LONG) -> Problem:
     """Three-level Lambda medium: levels (0, 1.5e-20, 1.9e-20) J, dipoles
     1-3 = 1e-29 and 2-3 = 0.8e-29 C m; decays 3->1 and 3->2 at 1/(2 T1);
     dephasing |k><k| so the optical coherences decay at 1/T2; probe sech at
@@ -306,11 +317,11 @@ def lambda_3lvl(n_cells=262_144, n_steps=100_000, tau=100e-15, t0=600e-15,
         if in_medium(c, n_cells):
             probes += [Probe(c, Q_RHO_RE, k, k) for k in range(n)]
     return Problem("lambda_3lvl", [qm], mats, regs, length, n_cells, n_steps=n_steps,
-                   sources=srcs, probes=probes)
+                   sources=srcs, probes=probes, courant=courant)
 
 
 def ladder_6lvl(n_cells=131_072, n_steps=50_000, seed=3, tau=10e-15, t0=60e-15,
-                decay=1e11, dephase=1e12) -> Problem:
+                decay=1e11, dephase=1e12, courant=COURANT_LONG) -> Problem:
     """Seeded six-level medium: H0 = diag(0, sorted U(0, 5e-20) J x 5),
     mu real symmetric with zero diagonal and N(0, (1e-29)^2) off-diagonals,
     decays |k-1><k| (k = 2..6) and |1><6|, dephasing |k><k|; sech pulse at the
@@ -341,7 +352,7 @@ def ladder_6lvl(n_cells=131_072, n_steps=50_000, seed=3, tau=10e-15, t0=60e-15,
         if in_medium(c, n_cells):
             probes += [Probe(c, Q_RHO_RE, k, k) for k in range(n)]
     return Problem("ladder_6lvl", [qm], mats, regs, length, n_cells, n_steps=n_steps,
-                   sources=[src], probes=probes)
+                   sources=[src], probes=probes, courant=courant)
 
 
 def batch_mixed(n_sims=512, seed=4, min_cells=1024, max_cells=65536,
@@ -360,7 +371,7 @@ def batch_mixed(n_sims=512, seed=4, min_cells=1024, max_cells=65536,
         fd, fw, f1, f2 = (1.0 + 0.2 * (2.0 * r[3 + k] - 1.0) for k in range(4))
         if r[0] < 0.5:
             p = sit_2lvl(n_cells=nx, n_steps=nt, t_end=0.0, density=1e24 * fd,
-                         omega0=2e14 * fw, gamma1=1e9 / f1, gamma2=1e9 / f2)
+                         omega0=2e14 * fw, gamma1=1e9 / f1, gamma2=1e9 / f2, courant=COURANT_LONG)
         else:
             p = lambda_3lvl(n_cells=nx, n_steps=nt, t1=10e-12 * f1, t2=1e-12 * f2)
             qm = p.qms[0]
