@@ -36,24 +36,26 @@ namespace dev {
 constexpr unsigned FULL = 0xffffffffu;
 
 // ------------------------------------------------------------- math helpers
+// |x| > 1/2: library sincos
+static __device__ __forceinline__ void sincos_m1_wide(float x, float &s, float &cm1) {
+  float c;
+  sincosf(x, &s, &c);
+  cm1 = c - 1.0f;
+}
+
 __device__ __forceinline__ void sincos_m1(float x, float &s, float &cm1) {
-  if (fabsf(x) <= 0.5f) {
-    const float t = x * x;
-    float ps = fmaf(t, 1.0f / 362880.0f, -1.0f / 5040.0f);
-    ps = fmaf(t, ps, 1.0f / 120.0f);
-    ps = fmaf(t, ps, -1.0f / 6.0f);
-    ps = fmaf(t, ps, 1.0f);
-    s = x * ps;
-    float pc = fmaf(t, -1.0f / 3628800.0f, 1.0f / 40320.0f);
-    pc = fmaf(t, pc, -1.0f / 720.0f);
-    pc = fmaf(t, pc, 1.0f / 24.0f);
-    pc = fmaf(t, pc, -0.5f);
-    cm1 = t * pc;
-  } else {
-    float c;
-    sincosf(x, &s, &c);
-    cm1 = c - 1.0f;
-  }
+  const float t = x * x;
+  float ps = fmaf(t, 1.0f / 362880.0f, -1.0f / 5040.0f);
+  ps = fmaf(t, ps, 1.0f / 120.0f);
+  ps = fmaf(t, ps, -1.0f / 6.0f);
+  ps = fmaf(t, ps, 1.0f);
+  s = x * ps;
+  float pc = fmaf(t, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+  pc = fmaf(t, pc, -1.0f / 720.0f);
+  pc = fmaf(t, pc, 1.0f / 24.0f);
+  pc = fmaf(t, pc, -0.5f);
+  cm1 = t * pc;
+  if (fabsf(x) > 0.5f) sincos_m1_wide(x, s, cm1);
 }
 
 __device__ __forceinline__ void sincos_m1(double x, double &s, double &cm1) {
@@ -287,8 +289,25 @@ __device__ __forceinline__ void ff_add(float &h, float &l, float a, float b) {
   l = e - (h - s);
 }
 
+// (h, l) += (a, b) without renormalising: h takes the rounded sum of the
+// high words, l collects the exact rounding error and the low words.  The
+// pair stays exact; |l| grows by at most an ulp of h per update, and the
+// tiled kernel renormalises once per tile.
+__device__ __forceinline__ void ff_add_lazy(float &h, float &l, float a, float b) {
+  float s, e;
+  two_sum(h, a, s, e);
+  l = e + (l + b);
+  h = s;
+}
+
+__device__ __forceinline__ void ff_renorm(float &h, float &l) {
+  const float s = h + l;
+  l = l - (s - h);
+  h = s;
+}
+
 // f += c (xr - xl) + extra   (extra: a small correction added to the low part)
-template <typename real>
+template <typename real, bool LAZY = false>
 __device__ __forceinline__ void fld_axpy_diff(real &fh, real &fl, real c, real xrh, real xrl, real xlh, real xll,
                                               real extra) {
   if constexpr (sizeof(real) == 8) {
@@ -298,20 +317,26 @@ __device__ __forceinline__ void fld_axpy_diff(real &fh, real &fl, real c, real x
     two_sum(xrh, -xlh, dh, de);
     const float dl = de + (xrl - xll);
     two_prod(c, dh, ph, pe);
-    ff_add(fh, fl, ph, pe + c * dl + extra);
+    if (LAZY)
+      ff_add_lazy(fh, fl, ph, pe + c * dl + extra);
+    else
+      ff_add(fh, fl, ph, pe + c * dl + extra);
   }
 }
 
 // f += (xr - xl) + extra: the unit-coefficient case (vacuum-like media at
 // Courant number 1, where the FP32 coefficients round to exactly 1 and 0)
-template <typename real>
+template <typename real, bool LAZY = false>
 __device__ __forceinline__ void fld_add_diff(real &fh, real &fl, real xrh, real xrl, real xlh, real xll, real extra) {
   if constexpr (sizeof(real) == 8) {
     fh += (xrh - xlh) + extra;
   } else {
     float dh, de;
     two_sum(xrh, -xlh, dh, de);
-    ff_add(fh, fl, dh, de + (xrl - xll) + extra);
+    if (LAZY)
+      ff_add_lazy(fh, fl, dh, de + (xrl - xll) + extra);
+    else
+      ff_add(fh, fl, dh, de + (xrl - xll) + extra);
   }
 }
 
@@ -526,9 +551,10 @@ __device__ __forceinline__ void st_row<double, 4>(double *p, const double (&v)[4
 //   PM = 0: step operator of the lane's medium from shared memory;
 //   PM = 1: dense per-cell step operator rows in registers (jittered media);
 //   PM = 2: structured two-level per-cell rows in registers (see PrmBloch2).
-//   UNIT: all field coefficients are exactly 1 (and a' - 1 = 0); cells
-//         outside the grid are then held at zero explicitly.
-template <typename real, int N, int R, bool KAHAN, int PM, bool UNIT>
+// The time loop has no per-cell branches: cells are interleaved by the
+// scheduler only inside one basic block, so vacuum cells run the Bloch step
+// with a zero field angle and a zero coupling instead of being skipped.
+template <typename real, int N, int R, bool KAHAN, int PM>
 __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int nsteps, int T, int cur) {
   constexpr int K = N * N - 1;
   constexpr bool FF = sizeof(real) == 4;
@@ -542,6 +568,10 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
   for (int i = threadIdx.x; i < a.n_slot * a.qstride; i += blockDim.x) s_q[i] = reinterpret_cast<const real *>(a.qpar)[i];
   for (int i = threadIdx.x; i < a.n_mat_all; i += blockDim.x) s_slot[i] = a.qslot[i];
   __syncthreads();
+  // this thread's slot for the rotated state of its probe cells
+  real *s_u = reinterpret_cast<real *>(reinterpret_cast<unsigned char *>(s_slot) +
+                                       ((sizeof(int) * a.n_mat_all + 15) / 16) * 16) +
+              (size_t)threadIdx.x * R * K;
 
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -558,7 +588,7 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
   const int g0 = tb + lane * R;         // first cell of this lane
   const int base = a.off + g0;          // its array index (>= 0, multiple of R)
 
-  real E[R], El[R], H[R], Hl[R], ca[R], cb[R], ch[R];
+  real E[R], El[R], H[R], Hl[R];
   real d[K][R], cc[K][R];
   ld_row<real, R>(reinterpret_cast<const real *>(a.E[cur]) + base, E);
   ld_row<real, R>(reinterpret_cast<const real *>(a.H[cur]) + base, H);
@@ -579,6 +609,8 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
 #pragma unroll
       for (int j = 0; j < R; ++j) cc[i][j] = real(0);
   }
+  // field coefficients per cell (pad cells outside the grid have zeros)
+  real ca[R], cb[R], ch[R], mk[R];
   unsigned med = 0;
   int slot = -1;
 #pragma unroll
@@ -588,11 +620,13 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
     cb[j] = s_emc[mt * 4 + 1];
     ch[j] = (g0 + j == 0) ? real(0) : s_emc[mt * 4 + 2];   // face 0 is a fixed boundary slot
     const int sl = s_slot[mt];
+    mk[j] = sl >= 0 ? real(1) : real(0);
     if (sl >= 0) {
       med |= 1u << j;
       slot = sl;
     }
   }
+  const bool warp_med = __any_sync(FULL, med != 0);
   const real *mb = s_q + (slot < 0 ? 0 : slot) * a.qstride;
 
   PrmReg<real, N> pr[PERCELL ? R : 1];
@@ -611,7 +645,6 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
       pr[j].ww0 = pc[(size_t)(K * K + 2 * K) * a.ld + base + j];
     }
   }
-
   PrmBloch2<real> b2[PM == 2 ? R : 1];
   if constexpr (PM == 2) {
     const real *pc = reinterpret_cast<const real *>(a.pcell2);
@@ -627,11 +660,6 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
       b2[j].w2c = pc[(size_t)6 * a.ld + base + j];
     }
   }
-  unsigned inside = 0;   // cells of the grid (UNIT mode keeps the others at zero)
-#pragma unroll
-  for (int j = 0; j < R; ++j)
-    if (g0 + j >= 0 && g0 + j < a.nx) inside |= 1u << j;
-
   // warp-uniform: does the tile touch a source, a boundary cell, a probe?
   const int t_lo = tb, t_hi = tb + 32 * R;   // [t_lo, t_hi)
   bool any_src = false;
@@ -652,20 +680,13 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
 #pragma unroll 1
   for (int t = 0; t < nsteps; ++t) {
     const long long n = n0 + t;
-    // ---- H^{n+1/2} on the left faces of my cells
-    const real elh = __shfl_up_sync(FULL, E[R - 1], 1);
-    const real ell = FF ? __shfl_up_sync(FULL, El[R - 1], 1) : real(0);
-    real Hn[R], Hln[R];
+    // ---- H^{n+1/2} on the left faces of my cells (in place)
+    {
+      const real elh = __shfl_up_sync(FULL, E[R - 1], 1);
+      const real ell = FF ? __shfl_up_sync(FULL, El[R - 1], 1) : real(0);
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-      Hn[j] = H[j];
-      Hln[j] = Hl[j];
-      if constexpr (UNIT) {
-        if ((inside & (1u << j)) && g0 + j != 0)   // face 0 is a fixed boundary slot
-          fld_add_diff<real>(Hn[j], Hln[j], E[j], El[j], j ? E[j - 1] : elh, j ? El[j - 1] : ell, real(0));
-      } else {
-        fld_axpy_diff<real>(Hn[j], Hln[j], ch[j], E[j], El[j], j ? E[j - 1] : elh, j ? El[j - 1] : ell, real(0));
-      }
+      for (int j = R - 1; j >= 0; --j)
+        fld_axpy_diff<real, true>(H[j], Hl[j], ch[j], E[j], El[j], j ? E[j - 1] : elh, j ? El[j - 1] : ell, real(0));
     }
     if (any_src) {
       for (int s = 0; s < a.n_src; ++s) {
@@ -675,57 +696,84 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
           if (f == j) {
             real vh, vl;
             src_val<real>(a.src[s].sH, n, a.nt, vh, vl);
-            fld_add<real>(Hn[j], Hln[j], vh, vl);
+            fld_add<real>(H[j], Hl[j], vh, vl);
           }
       }
     }
-    // ---- rho^{n+1/2} and the coupling term
+    // ---- rho^{n+1/2} and the coupling term (all cells of a warp that holds
+    // any medium; vacuum cells see a zero angle and contribute no current)
     real pw[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-      pw[j] = real(0);
-      if (med & (1u << j)) {
+    for (int j = 0; j < R; ++j) pw[j] = real(0);
+    if (warp_med) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
         real dj[K], cj[K], u[K];
 #pragma unroll
         for (int i = 0; i < K; ++i) {
           dj[i] = d[i][j];
           cj[i] = cc[i][j];
         }
-        const real ej = fld_val<real>(E[j], El[j]);
+        const real ej = fld_val<real>(E[j], El[j]) * mk[j];
+        real q;
         if constexpr (PM == 2)
-          pw[j] = bloch_step_b2<real, KAHAN>(b2[j], ej, dj, cj, u);
+          q = bloch_step_b2<real, KAHAN>(b2[j], ej, dj, cj, u);
         else if constexpr (PM == 1)
-          pw[j] = bloch_step<real, N, KAHAN>(pr[PERCELL ? j : 0], ej, dj, cj, u);
+          q = bloch_step<real, N, KAHAN>(pr[PERCELL ? j : 0], ej, dj, cj, u);
         else
-          pw[j] = bloch_step<real, N, KAHAN>(PrmBlock<real, N>{mb}, ej, dj, cj, u);
+          q = bloch_step<real, N, KAHAN>(PrmBlock<real, N>{mb}, ej, dj, cj, u);
+        pw[j] = q * mk[j];
 #pragma unroll
         for (int i = 0; i < K; ++i) {
           d[i][j] = dj[i];
           cc[i][j] = cj[i];
         }
-        if (pmask & (1u << j)) {
-          for (int p = 0; p < a.n_probe; ++p)
-            if (a.pr_cell[p] == g0 + j && a.pr_q[p] >= 2)
-              rec[(size_t)p * a.nt + n] = probe_rho<real, N>(pcoef + (size_t)p * (K + 1), u);
+        if (pmask & (1u << j))   // park u of probe cells (predicated stores)
+#pragma unroll
+          for (int i = 0; i < K; ++i) s_u[j * K + i] = u[i];
+      }
+      if (any_probe && pmask) {
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+          if (pmask & (1u << j)) {
+            real u[K];
+#pragma unroll
+            for (int i = 0; i < K; ++i) u[i] = s_u[j * K + i];
+            for (int p = 0; p < a.n_probe; ++p)
+              if (a.pr_cell[p] == g0 + j && a.pr_q[p] >= 2)
+                rec[(size_t)p * a.nt + n] = probe_rho<real, N>(pcoef + (size_t)p * (K + 1), u);
+          }
+      }
+    }
+    // ---- boundary cells: keep E^n of the boundary cell and its neighbour
+    real bo_h = real(0), bo_l = real(0), no_h = real(0), no_l = real(0);
+    if (any_bnd) {
+      const real r_oh = __shfl_down_sync(FULL, E[0], 1), r_ol = __shfl_down_sync(FULL, El[0], 1);
+      const real l_oh = __shfl_up_sync(FULL, E[R - 1], 1), l_ol = __shfl_up_sync(FULL, El[R - 1], 1);
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        if (g0 + j == 0) {
+          bo_h = E[j];
+          bo_l = El[j];
+          no_h = j < R - 1 ? E[j + 1] : r_oh;
+          no_l = j < R - 1 ? El[j + 1] : r_ol;
+        }
+        if (g0 + j == a.nx - 1) {
+          bo_h = E[j];
+          bo_l = El[j];
+          no_h = j ? E[j - 1] : l_oh;
+          no_l = j ? El[j - 1] : l_ol;
         }
       }
     }
-    // ---- E^{n+1}
-    const real hrh = __shfl_down_sync(FULL, Hn[0], 1);
-    const real hrl = FF ? __shfl_down_sync(FULL, Hln[0], 1) : real(0);
-    real En[R], Eln[R];
+    // ---- E^{n+1} (in place)
+    {
+      const real hrh = __shfl_down_sync(FULL, H[0], 1);
+      const real hrl = FF ? __shfl_down_sync(FULL, Hl[0], 1) : real(0);
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-      En[j] = E[j];
-      Eln[j] = El[j];
-      if constexpr (UNIT) {
-        if (inside & (1u << j))
-          fld_add_diff<real>(En[j], Eln[j], j < R - 1 ? Hn[j + 1] : hrh, j < R - 1 ? Hln[j + 1] : hrl, Hn[j], Hln[j],
-                             -pw[j]);
-      } else {
-        fld_axpy_diff<real>(En[j], Eln[j], cb[j], j < R - 1 ? Hn[j + 1] : hrh, j < R - 1 ? Hln[j + 1] : hrl, Hn[j],
-                            Hln[j], ca[j] * E[j] - pw[j]);
-      }
+      for (int j = 0; j < R; ++j)
+        fld_axpy_diff<real, true>(E[j], El[j], cb[j], j < R - 1 ? H[j + 1] : hrh, j < R - 1 ? Hl[j + 1] : hrl, H[j],
+                                  Hl[j], ca[j] * E[j] - pw[j]);
     }
     if (any_src) {
       for (int s = 0; s < a.n_src; ++s) {
@@ -736,55 +784,40 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
             real vh, vl;
             src_val<real>(a.src[s].sE, n, a.nt, vh, vl);
             if (a.src[s].kind == 2) {
-              En[j] = vh;
-              Eln[j] = vl;
+              E[j] = vh;
+              El[j] = vl;
             } else {
-              fld_add<real>(En[j], Eln[j], vh, vl);
+              fld_add<real>(E[j], El[j], vh, vl);
             }
           }
       }
     }
     if (any_bnd) {
-      // neighbours' old and new E across lane borders
-      const real r_oh = __shfl_down_sync(FULL, E[0], 1), r_ol = __shfl_down_sync(FULL, El[0], 1);
-      const real r_nh = __shfl_down_sync(FULL, En[0], 1), r_nl = __shfl_down_sync(FULL, Eln[0], 1);
-      const real l_oh = __shfl_up_sync(FULL, E[R - 1], 1), l_ol = __shfl_up_sync(FULL, El[R - 1], 1);
-      const real l_nh = __shfl_up_sync(FULL, En[R - 1], 1), l_nl = __shfl_up_sync(FULL, Eln[R - 1], 1);
+      // E_b^{n+1} = E_nb^n + k (E_nb^{n+1} - E_b^n), or 0 for a mirror
+      const real r_nh = __shfl_down_sync(FULL, E[0], 1), r_nl = __shfl_down_sync(FULL, El[0], 1);
+      const real l_nh = __shfl_up_sync(FULL, E[R - 1], 1), l_nl = __shfl_up_sync(FULL, El[R - 1], 1);
       real Bh[R], Bl[R];
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        Bh[j] = En[j];
-        Bl[j] = Eln[j];
-      }
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
+        Bh[j] = E[j];
+        Bl[j] = El[j];
         const bool lft = g0 + j == 0, rgt = g0 + j == a.nx - 1;
         if (lft || rgt) {
-          real oh, ol, nh, nl;
-          if (lft) {
-            oh = j < R - 1 ? E[j + 1] : r_oh;
-            ol = j < R - 1 ? El[j + 1] : r_ol;
-            nh = j < R - 1 ? En[j + 1] : r_nh;
-            nl = j < R - 1 ? Eln[j + 1] : r_nl;
-          } else {
-            oh = j ? E[j - 1] : l_oh;
-            ol = j ? El[j - 1] : l_ol;
-            nh = j ? En[j - 1] : l_nh;
-            nl = j ? Eln[j - 1] : l_nl;
-          }
+          const real nh = lft ? (j < R - 1 ? E[j + 1] : r_nh) : (j ? E[j - 1] : l_nh);
+          const real nl = lft ? (j < R - 1 ? El[j + 1] : r_nl) : (j ? El[j - 1] : l_nl);
           if ((lft ? a.bc_l : a.bc_r) == 1) {
             Bh[j] = Bl[j] = real(0);
           } else {
-            Bh[j] = oh;
-            Bl[j] = ol;
-            fld_axpy_diff<real>(Bh[j], Bl[j], real(lft ? a.kmur_l : a.kmur_r), nh, nl, E[j], El[j], real(0));
+            Bh[j] = no_h;
+            Bl[j] = no_l;
+            fld_axpy_diff<real>(Bh[j], Bl[j], real(lft ? a.kmur_l : a.kmur_r), nh, nl, bo_h, bo_l, real(0));
           }
         }
       }
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        En[j] = Bh[j];
-        Eln[j] = Bl[j];
+        E[j] = Bh[j];
+        El[j] = Bl[j];
       }
     }
     if (any_probe && pmask) {
@@ -793,20 +826,20 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
         if (pmask & (1u << j))
           for (int p = 0; p < a.n_probe; ++p)
             if (a.pr_cell[p] == g0 + j && a.pr_q[p] < 2)
-              rec[(size_t)p * a.nt + n] = a.pr_q[p] == 0 ? fld_val<real>(En[j], Eln[j]) : fld_val<real>(Hn[j], Hln[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-      E[j] = En[j];
-      El[j] = Eln[j];
-      H[j] = Hn[j];
-      Hl[j] = Hln[j];
+              rec[(size_t)p * a.nt + n] = a.pr_q[p] == 0 ? fld_val<real>(E[j], El[j]) : fld_val<real>(H[j], Hl[j]);
     }
   }
 
   // ---- write back the owned cells (never past the last cell)
   const bool owned = ti0 >= T && ti0 < 32 * R - T;   // T is a multiple of R
   if (!owned) return;
+  if constexpr (FF) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      ff_renorm(E[j], El[j]);
+      ff_renorm(H[j], Hl[j]);
+    }
+  }
   real *Eo = reinterpret_cast<real *>(a.E[cur ^ 1]);
   real *Ho = reinterpret_cast<real *>(a.H[cur ^ 1]);
   real *Elo = reinterpret_cast<real *>(a.El[cur ^ 1]);
@@ -970,14 +1003,15 @@ int plain_step_impl(const Args &a, long long n, int cur, cudaStream_t st) {
   return (int)cudaGetLastError();
 }
 
-template <typename real, int N, int R, bool KAHAN, int PM, bool UNIT>
+template <typename real, int N, int R, bool KAHAN, int PM>
 int tiled_impl(const Args &a, long long n0, int nsteps, int T, int cur, cudaStream_t st) {
   const int own = 32 * R - 2 * T;
   const int n_warps = (a.nx + own - 1) / own;
   const int bs = 128, wpb = bs / 32;
   const int gs = (n_warps + wpb - 1) / wpb;
-  const size_t sm = sizeof(real) * (a.n_mat_all * 4 + a.n_slot * a.qstride) + sizeof(int) * a.n_mat_all + 16;
-  k_tiled<real, N, R, KAHAN, PM, UNIT><<<gs, bs, sm, st>>>(a, n0, nsteps, T, cur);
+  const size_t sm = sizeof(real) * (a.n_mat_all * 4 + a.n_slot * a.qstride) +
+                    ((sizeof(int) * a.n_mat_all + 15) / 16) * 16 + sizeof(real) * (size_t)bs * R * (N * N - 1) + 16;
+  k_tiled<real, N, R, KAHAN, PM><<<gs, bs, sm, st>>>(a, n0, nsteps, T, cur);
   return (int)cudaGetLastError();
 }
 

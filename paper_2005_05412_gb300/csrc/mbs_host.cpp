@@ -403,7 +403,7 @@ struct mbs_scenario_s {
   // FP64 master copies
   std::vector<double> emc, qpar, pcell, pcell2, Dinit, pr_coef, zref;
   bool has_b2 = false;   // structured two-level rows available (pcell2)
-  bool unit32 = false;   // every field coefficient rounds to exactly 1 (a' - 1 to 0) in FP32
+
   std::vector<int> qslot, pr_cell, pr_q;
   std::vector<SrcHost> src;
   double kmur_l = 0, kmur_r = 0;
@@ -730,7 +730,7 @@ mbs::Args make_args(mbs_scenario_s *s, int prec) {
   a.qstride = s->qstride;
   a.pcell = s->has_pcell ? b.pcell : nullptr;
   a.pcell2 = s->has_b2 ? b.pcell2 : nullptr;
-  a.unit = (prec == 1 && s->unit32) ? 1 : 0;
+
   a.n_src = (int)s->src.size();
   for (size_t k = 0; k < s->src.size(); ++k) {
     a.src[k].kind = s->src[k].kind;
@@ -1039,18 +1039,6 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
     s->has_b2 = bad2 == 0;
     if (!s->has_b2) s->pcell2.clear();
   }
-  // unit field coefficients in FP32
-  {
-    bool unit = true;
-    std::vector<char> used(n_mat, 0);
-    for (int m = 0; m < nx; ++m) used[dev->cell_mat[m]] = 1;
-    for (int i = 0; i < n_mat; ++i)
-      if (used[i])
-        unit = unit && (float)s->emc[i * 4 + 0] == 0.0f && (float)s->emc[i * 4 + 1] == 1.0f &&
-               (float)s->emc[i * 4 + 2] == 1.0f;
-    s->unit32 = unit;
-  }
-
   // sources
   for (int k = 0; k < n_src; ++k) {
     const mbs_source &sr = src[k];

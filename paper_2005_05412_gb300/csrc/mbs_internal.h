@@ -75,7 +75,7 @@ struct Args {
   int n_slot, qstride;
   const void *pcell;           // [pc_rows][ld] per-cell parameters or null
   const void *pcell2;          // [7][ld] structured two-level rows (see PrmBloch2) or null
-  int unit;                    // 1: every field coefficient is exactly 1 in this precision
+
   int n_src;
   SrcDev src[MAXSRC];
   int bc_l, bc_r;              // 0 = Mur, 1 = PEC
