@@ -156,18 +156,26 @@ enum { MBS_ALGO_AUTO = 0,
                                   with halo recompute (the redundant-calculation
                                   loop of Sec. 3.2) */
 
+enum { MBS_SOLVE_ONE_AT_A_TIME = 1 };  /* flags: solve batch members one after another */
+
 typedef struct {
     int precision;     /* MBS_PREC_* */
     int algo;          /* MBS_ALGO_* */
     int tile_steps;    /* steps per tiled launch (multiple of 4), 0 = default (12) */
     int check_every;   /* steps between device-side state checks, 0 = only at the end */
+    int flags;         /* MBS_SOLVE_* */
 } mbs_opts;
 
 /* Run every scenario from its initial condition to its last step (previous
  * results are discarded).  `cuda_stream` is a cudaStream_t or NULL for the
  * legacy default stream.  The call returns after the work has completed.
+ * Several scenarios on the tiled path (algo AUTO or TILED, check_every 0, no
+ * MBS_SOLVE_ONE_AT_A_TIME) advance together: each round of tile_steps steps
+ * is one launch per kernel variant over the blocks of all scenarios still
+ * running (scenarios may differ in cells, levels, steps and parameters).
  * Returns MBS_E_NUMERIC if a state check found a non-finite value or a
- * density-matrix eigenvalue below -1e-6. */
+ * density-matrix eigenvalue below -1e-6 (in a batch: the first such status,
+ * after every member has finished). */
 int mbs_solve(mbs_scenario_t *batch, int n_scen, const mbs_opts *opts, void *cuda_stream);
 
 /* Copy probe `probe`'s trace (n_steps doubles, SI units) into out.  With

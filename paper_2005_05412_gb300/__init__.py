@@ -67,7 +67,11 @@ class _Probe(C.Structure):
 
 
 class _Opts(C.Structure):
-    _fields_ = [("precision", C.c_int), ("algo", C.c_int), ("tile_steps", C.c_int), ("check_every", C.c_int)]
+    _fields_ = [("precision", C.c_int), ("algo", C.c_int), ("tile_steps", C.c_int), ("check_every", C.c_int),
+                ("flags", C.c_int)]
+
+
+MBS_SOLVE_ONE_AT_A_TIME = 1
 
 
 _lib = None
@@ -207,14 +211,17 @@ def mbs_scenario(device: Device, dt=0.0, courant=1.0, t_end=0.0, n_steps=0, sour
     return Scenario(h.value, device, len(probes))
 
 
-def mbs_solve(scenarios, precision="fp32", algo="auto", tile_steps=0, check_every=0, stream=None):
-    """Run every scenario to its end.  stream: a cudaStream_t handle (int),
-    e.g. torch.cuda.current_stream().cuda_stream, or None."""
+def mbs_solve(scenarios, precision="fp32", algo="auto", tile_steps=0, check_every=0, stream=None,
+              one_at_a_time=False):
+    """Run every scenario to its end (a batch advances together unless
+    one_at_a_time).  stream: a cudaStream_t handle (int), e.g.
+    torch.cuda.current_stream().cuda_stream, or None."""
     if isinstance(scenarios, Scenario):
         scenarios = [scenarios]
     arr = (C.c_void_p * len(scenarios))(*[s.handle for s in scenarios])
     o = _Opts(PREC[precision] if isinstance(precision, str) else int(precision),
-              ALGO[algo] if isinstance(algo, str) else int(algo), int(tile_steps), int(check_every))
+              ALGO[algo] if isinstance(algo, str) else int(algo), int(tile_steps), int(check_every),
+              MBS_SOLVE_ONE_AT_A_TIME if one_at_a_time else 0)
     return _check(lib().mbs_solve(arr, len(scenarios), C.byref(o), None if stream is None else C.c_void_p(int(stream))))
 
 

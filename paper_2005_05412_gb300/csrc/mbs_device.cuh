@@ -555,12 +555,12 @@ __device__ __forceinline__ void st_row<double, 4>(double *p, const double (&v)[4
 // scheduler only inside one basic block, so vacuum cells run the Bloch step
 // with a zero field angle and a zero coupling instead of being skipped.
 template <typename real, int N, int R, bool KAHAN, int PM>
-__global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int nsteps, int T, int cur) {
+__device__ __forceinline__ void tile_body(const Args &a, const int warp, long long n0, int nsteps, int T, int cur,
+                                          unsigned char *smem_raw) {
   constexpr int K = N * N - 1;
   constexpr bool FF = sizeof(real) == 4;
   constexpr bool PERCELL = PM == 1;
   static_assert(PM != 2 || N == 2, "structured rows are two-level");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   real *s_emc = reinterpret_cast<real *>(smem_raw);
   real *s_q = s_emc + a.n_mat_all * 4;
   int *s_slot = reinterpret_cast<int *>(s_q + a.n_slot * a.qstride);
@@ -574,7 +574,6 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
               (size_t)threadIdx.x * R * K;
 
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int own = 32 * R - 2 * T;
   int c_own = warp * own;
   if (c_own >= a.nx) return;   // whole warp leaves together
@@ -877,6 +876,29 @@ __global__ void __launch_bounds__(128) k_tiled(const Args a, long long n0, int n
   }
 }
 
+// One simulation: warp w of the grid is warp w of the simulation.
+template <typename real, int N, int R, bool KAHAN, int PM>
+__global__ void __launch_bounds__(128) k_tiled(const __grid_constant__ Args a, long long n0, int nsteps, int T, int cur) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  tile_body<real, N, R, KAHAN, PM>(a, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, n0, nsteps, T, cur, smem_raw);
+}
+
+// A batch of simulations in one launch: block b works for simulation
+// tasks[b].x, starting at that simulation's warp tasks[b].y (all warps of a
+// block belong to one simulation).  Every simulation starts at step 0, so
+// step n0 is common; finished simulations return at once.
+template <typename real, int N, int R, bool KAHAN, int PM>
+__global__ void __launch_bounds__(128) k_tiled_batch(const Args *__restrict__ args, const int2 *__restrict__ tasks,
+                                                     long long n0, int T, int cur) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 tk = tasks[blockIdx.x];
+  const Args &a = args[tk.x];
+  if (n0 >= a.nt) return;   // the whole block leaves together
+  const int nsteps = (int)(a.nt - n0 < (long long)T ? a.nt - n0 : (long long)T);
+  tile_body<real, N, R, KAHAN, PM>(a, tk.y + (int)(threadIdx.x >> 5), n0, nsteps, T, cur, smem_raw);
+}
+
+
 // ========================================================= state check
 // Number of negative pivots of the LDL^H factorisation of A - sigma I (no
 // pivoting): by Sylvester's law of inertia, the number of eigenvalues of the
@@ -1003,15 +1025,29 @@ int plain_step_impl(const Args &a, long long n, int cur, cudaStream_t st) {
   return (int)cudaGetLastError();
 }
 
+// dynamic shared memory of a tiled block: tables + per-thread probe slots
+template <typename real, int N, int R>
+size_t tiled_smem(int n_mat_all, int n_slot, int qstride) {
+  return sizeof(real) * (n_mat_all * 4 + n_slot * qstride) + ((sizeof(int) * n_mat_all + 15) / 16) * 16 +
+         sizeof(real) * (size_t)128 * R * (N * N - 1) + 16;
+}
+
 template <typename real, int N, int R, bool KAHAN, int PM>
 int tiled_impl(const Args &a, long long n0, int nsteps, int T, int cur, cudaStream_t st) {
   const int own = 32 * R - 2 * T;
   const int n_warps = (a.nx + own - 1) / own;
   const int bs = 128, wpb = bs / 32;
   const int gs = (n_warps + wpb - 1) / wpb;
-  const size_t sm = sizeof(real) * (a.n_mat_all * 4 + a.n_slot * a.qstride) +
-                    ((sizeof(int) * a.n_mat_all + 15) / 16) * 16 + sizeof(real) * (size_t)bs * R * (N * N - 1) + 16;
+  const size_t sm = tiled_smem<real, N, R>(a.n_mat_all, a.n_slot, a.qstride);
   k_tiled<real, N, R, KAHAN, PM><<<gs, bs, sm, st>>>(a, n0, nsteps, T, cur);
+  return (int)cudaGetLastError();
+}
+
+template <typename real, int N, int R, bool KAHAN, int PM>
+int tiled_batch_impl(const Args *args, const int2 *tasks, int n_tasks, size_t smem, long long n0, int T, int cur,
+                     cudaStream_t st) {
+  if (n_tasks <= 0) return 0;
+  k_tiled_batch<real, N, R, KAHAN, PM><<<n_tasks, 128, smem, st>>>(args, tasks, n0, T, cur);
   return (int)cudaGetLastError();
 }
 

@@ -1153,8 +1153,9 @@ int mbs_scenario_info(mbs_scenario_t s, double *dt, double *dz, long long *n_ste
   return MBS_OK;
 }
 
-static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
-  const int prec = o.precision;
+// Upload the precision's tables on first use and reset the state to the
+// initial condition (all asynchronous on `st`).
+static int prepare_solve(mbs_scenario_s *s, int prec, cudaStream_t st) {
   g_h2d = &s->h2d_bytes;
   int rc = ensure_bundle(s, prec);
   g_h2d = nullptr;
@@ -1176,63 +1177,47 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMemsetAsync(b.pd, 0, row, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_flags, 0, 4 * sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(e, "state reset");
-  mbs::Args a = make_args(s, prec);
+  return MBS_OK;
+}
 
-  int algo = o.algo;
-  if (algo == MBS_ALGO_AUTO) algo = mbs::tiled_supported(prec, s->N) && (!s->has_pcell || s->N == 2) ? MBS_ALGO_TILED : MBS_ALGO_PLAIN;
-  int T = o.tile_steps > 0 ? o.tile_steps : 12;
-  const int chk = o.check_every > 0 ? o.check_every : 0;
-  const int nchk = (int)s->chk_cells.size();
-  int cur = 0;
-  auto check = [&](int c) -> int {
-    if (!nchk) return 0;
-    ++s->launches;
-    return mbs::launch_check(a, c, s->d_chk_cells, nchk, s->d_chk_min, s->d_chk_tr, s->d_zref, nullptr, st);
-  };
-  if (algo == MBS_ALGO_TILED) {
-    if (!mbs::tiled_supported(prec, s->N) || (s->has_pcell && s->N != 2))
-      return fail(MBS_E_INVALID, "tiled kernels cover N = 2 (also with per-cell factors) and N = 3");
-    const int R = s->N == 2 ? 4 : 2;
-    if (T % 4 != 0 || T < 4 || 32 * R - 2 * T < 8)
-      return fail(MBS_E_INVALID, "tile_steps must be a multiple of 4 in [4, %d]", (32 * R - 8) / 2);
-    // each lane's R-cell group must hold at most one medium material
-    for (int g = 0; g * R < s->dev->nx; ++g) {
-      int sl = -1;
-      for (int j = 0; j < R && g * R + j < s->dev->nx; ++j) {
-        const int q = s->qslot[s->dev->cell_mat[g * R + j]];
-        if (q >= 0 && sl >= 0 && q != sl)
-          return fail(MBS_E_INVALID, "two media meet inside a %d-cell group; use the plain algorithm", R);
-        if (q >= 0) sl = q;
-      }
-    }
-    long long done = 0;
-    while (done < s->nt) {
-      const int ns = (int)std::min<long long>(T, s->nt - done);
-      int r = mbs::launch_tiled(a, done, ns, T, cur, st);
-      ++s->launches;
-      if (r) return cuda_fail((cudaError_t)r, "tiled launch");
-      cur ^= 1;
-      done += ns;
-      if (chk && done < s->nt && (done / chk) != ((done - ns) / chk))
-        if ((r = check(cur))) return cuda_fail((cudaError_t)r, "check launch");
-    }
-  } else {
-    for (long long n = 0; n < s->nt; ++n) {
-      int r = mbs::launch_plain_step(a, n, cur, st);
-      s->launches += 2;
-      if (r) return cuda_fail((cudaError_t)r, "plain launch");
-      cur ^= 1;
-      if (chk && (n + 1) % chk == 0 && n + 1 < s->nt)
-        if ((r = check(0))) return cuda_fail((cudaError_t)r, "check launch");
+static int default_algo(const mbs_scenario_s *s, int prec) {
+  return mbs::tiled_supported(prec, s->N) && (!s->has_pcell || s->N == 2) ? MBS_ALGO_TILED : MBS_ALGO_PLAIN;
+}
+
+// Whether the tiled kernels cover scenario s with tile depth T (sets the error).
+static int tiled_ok(const mbs_scenario_s *s, int prec, int T) {
+  if (!mbs::tiled_supported(prec, s->N) || (s->has_pcell && s->N != 2))
+    return fail(MBS_E_INVALID, "tiled kernels cover N = 2 (also with per-cell factors) and N = 3");
+  const int R = s->N == 2 ? 4 : 2;
+  if (T % 4 != 0 || T < 4 || 32 * R - 2 * T < 8)
+    return fail(MBS_E_INVALID, "tile_steps must be a multiple of 4 in [4, %d]", (32 * R - 8) / 2);
+  // each lane's R-cell group must hold at most one medium material
+  for (int g = 0; g * R < s->dev->nx; ++g) {
+    int sl = -1;
+    for (int j = 0; j < R && g * R + j < s->dev->nx; ++j) {
+      const int q = s->qslot[s->dev->cell_mat[g * R + j]];
+      if (q >= 0 && sl >= 0 && q != sl)
+        return fail(MBS_E_INVALID, "two media meet inside a %d-cell group; use the plain algorithm", R);
+      if (q >= 0) sl = q;
     }
   }
-  // plain: D, H live in buffer 0, E in `cur`; tiled: everything in `cur`
-  const int dcur = algo == MBS_ALGO_TILED ? cur : 0;
-  if ((rc = check(dcur))) return cuda_fail((cudaError_t)rc, "check launch");
-  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "solve");
+  return MBS_OK;
+}
+
+static int launch_state_check(mbs_scenario_s *s, const mbs::Args &a, int c, cudaStream_t st) {
+  const int nchk = (int)s->chk_cells.size();
+  if (!nchk) return 0;
+  ++s->launches;
+  return mbs::launch_check(a, c, s->d_chk_cells, nchk, s->d_chk_min, s->d_chk_tr, s->d_zref, nullptr, st);
+}
+
+// After the stream has drained: read the check results and device flags.
+static int finish_solve(mbs_scenario_s *s, int prec, int cur) {
+  cudaError_t e;
   s->solved_prec = prec;
   s->last_cur = cur;
   s->steps_run = s->nt;
+  const int nchk = (int)s->chk_cells.size();
   int flags[4] = {0, 0, 0, 0};
   if ((e = cudaMemcpy(flags, s->d_flags, sizeof flags, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e, "flags");
@@ -1256,16 +1241,174 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
   return MBS_OK;
 }
 
+static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
+  const int prec = o.precision;
+  int rc = prepare_solve(s, prec, st);
+  if (rc) return rc;
+  mbs::Args a = make_args(s, prec);
+  int algo = o.algo == MBS_ALGO_AUTO ? default_algo(s, prec) : o.algo;
+  const int T = o.tile_steps > 0 ? o.tile_steps : 12;
+  const int chk = o.check_every > 0 ? o.check_every : 0;
+  int cur = 0;
+  if (algo == MBS_ALGO_TILED) {
+    if ((rc = tiled_ok(s, prec, T))) return rc;
+    long long done = 0;
+    while (done < s->nt) {
+      const int ns = (int)std::min<long long>(T, s->nt - done);
+      int r = mbs::launch_tiled(a, done, ns, T, cur, st);
+      ++s->launches;
+      if (r) return cuda_fail((cudaError_t)r, "tiled launch");
+      cur ^= 1;
+      done += ns;
+      if (chk && done < s->nt && (done / chk) != ((done - ns) / chk))
+        if ((r = launch_state_check(s, a, cur, st))) return cuda_fail((cudaError_t)r, "check launch");
+    }
+  } else {
+    for (long long n = 0; n < s->nt; ++n) {
+      int r = mbs::launch_plain_step(a, n, cur, st);
+      s->launches += 2;
+      if (r) return cuda_fail((cudaError_t)r, "plain launch");
+      cur ^= 1;
+      if (chk && (n + 1) % chk == 0 && n + 1 < s->nt)
+        if ((r = launch_state_check(s, a, 0, st))) return cuda_fail((cudaError_t)r, "check launch");
+    }
+  }
+  // plain: D, H live in buffer 0, E in `cur`; tiled: everything in `cur`
+  const int dcur = algo == MBS_ALGO_TILED ? cur : 0;
+  if ((rc = launch_state_check(s, a, dcur, st))) return cuda_fail((cudaError_t)rc, "check launch");
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "solve");
+  return finish_solve(s, prec, cur);
+}
+
+// Batched tiled solve: every round launches, per kernel variant, one grid
+// over the blocks of all simulations still running, advancing them T steps.
+// Blocks are ordered by their simulation's step count (longest first), so
+// the running ones form a prefix and the grid shrinks as simulations end.
+static int solve_batch(std::vector<mbs_scenario_s *> &ss, const mbs_opts &o, cudaStream_t st) {
+  const int prec = o.precision;
+  const int T = o.tile_steps > 0 ? o.tile_steps : 12;
+  int rc;
+  for (auto *s : ss) {
+    if ((rc = prepare_solve(s, prec, st))) return rc;
+    if ((rc = tiled_ok(s, prec, T))) return rc;
+  }
+  struct Group {
+    int N, pm;
+    std::vector<int> sims;        // indices into ss, longest first
+    std::vector<int2> tasks;
+    std::vector<long long> task_nt;
+    int max_mat = 0, max_slot = 0, max_stride = 0;
+  };
+  std::vector<Group> groups;
+  std::vector<mbs::Args> args(ss.size());
+  for (size_t i = 0; i < ss.size(); ++i) {
+    args[i] = make_args(ss[i], prec);
+    const int pm = mbs::tiled_variant(args[i]);
+    if (pm < 0) return fail(MBS_E_INVALID, "scenario %zu is not covered by the tiled kernels", i);
+    Group *g = nullptr;
+    for (auto &x : groups)
+      if (x.N == ss[i]->N && x.pm == pm) g = &x;
+    if (!g) {
+      groups.push_back(Group{ss[i]->N, pm});
+      g = &groups.back();
+    }
+    g->sims.push_back((int)i);
+    g->max_mat = std::max(g->max_mat, args[i].n_mat_all);
+    g->max_slot = std::max(g->max_slot, args[i].n_slot);
+    g->max_stride = std::max(g->max_stride, args[i].qstride);
+  }
+  for (auto &g : groups) {
+    std::stable_sort(g.sims.begin(), g.sims.end(), [&](int x, int y) { return ss[x]->nt > ss[y]->nt; });
+    const int R = g.N == 2 ? 4 : 2, own = 32 * R - 2 * T;
+    for (int i : g.sims) {
+      const int n_warps = (ss[i]->dev->nx + own - 1) / own;
+      for (int w = 0; w < n_warps; w += 4) {
+        g.tasks.push_back(make_int2(i, w));
+        g.task_nt.push_back(ss[i]->nt);
+      }
+    }
+  }
+  // device copies of the per-simulation arguments and the block tasks
+  mbs::Args *d_args = nullptr;
+  std::vector<int2 *> d_tasks(groups.size(), nullptr);
+  cudaError_t e = cudaMalloc(&d_args, args.size() * sizeof(mbs::Args));
+  if (e == cudaSuccess) e = cudaMemcpy(d_args, args.data(), args.size() * sizeof(mbs::Args), cudaMemcpyHostToDevice);
+  for (size_t k = 0; k < groups.size() && e == cudaSuccess; ++k) {
+    e = cudaMalloc(&d_tasks[k], groups[k].tasks.size() * sizeof(int2));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(d_tasks[k], groups[k].tasks.data(), groups[k].tasks.size() * sizeof(int2),
+                     cudaMemcpyHostToDevice);
+  }
+  auto cleanup = [&]() {
+    cudaFree(d_args);
+    for (auto *p : d_tasks) cudaFree(p);
+  };
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "batch tables");
+  }
+  long long nt_max = 0;
+  for (auto *s : ss) nt_max = std::max(nt_max, s->nt);
+  int cur = 0;
+  for (long long n0 = 0; n0 < nt_max; n0 += T) {
+    for (size_t k = 0; k < groups.size(); ++k) {
+      const auto &g = groups[k];
+      // running blocks: a prefix of the tasks (sorted by step count)
+      const int active = (int)(std::upper_bound(g.task_nt.begin(), g.task_nt.end(), n0,
+                                                [](long long v, long long x) { return v > x; }) -
+                               g.task_nt.begin());
+      if (!active) continue;
+      const size_t smem = mbs::tiled_batch_smem(prec, g.N, g.max_mat, g.max_slot, g.max_stride);
+      const int r = mbs::launch_tiled_batch(prec, g.N, g.pm, d_args, d_tasks[k], active, smem, n0, T, cur, st);
+      if (r) {
+        cleanup();
+        return cuda_fail((cudaError_t)r, "batched tiled launch");
+      }
+    }
+    cur ^= 1;
+  }
+  // final state check of every simulation in its own final buffer
+  for (size_t i = 0; i < ss.size(); ++i) {
+    auto *s = ss[i];
+    const long long rounds = (s->nt + T - 1) / T;
+    s->launches = rounds;
+    if ((rc = launch_state_check(s, args[i], (int)(rounds % 2), st))) {
+      cleanup();
+      return cuda_fail((cudaError_t)rc, "check launch");
+    }
+  }
+  e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "batched solve");
+  int status = MBS_OK;
+  for (auto *s : ss) {
+    const long long rounds = (s->nt + T - 1) / T;
+    rc = finish_solve(s, prec, (int)(rounds % 2));
+    if (rc && status == MBS_OK) status = rc;
+  }
+  return status;
+}
+
 int mbs_solve(mbs_scenario_t *batch, int n_scen, const mbs_opts *opts, void *cuda_stream) {
   g_err.clear();
   if (!batch || n_scen < 1) return fail(MBS_E_INVALID, "empty batch");
-  mbs_opts o{MBS_PREC_FP32, MBS_ALGO_AUTO, 0, 0};
+  mbs_opts o{MBS_PREC_FP32, MBS_ALGO_AUTO, 0, 0, 0};
   if (opts) o = *opts;
   if (o.precision != MBS_PREC_FP64 && o.precision != MBS_PREC_FP32) return fail(MBS_E_INVALID, "bad precision");
   if (o.algo < 0 || o.algo > 2) return fail(MBS_E_INVALID, "bad algorithm");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
-  for (int i = 0; i < n_scen; ++i) {
+  for (int i = 0; i < n_scen; ++i)
     if (!batch[i]) return fail(MBS_E_INVALID, "scenario %d is NULL", i);
+  // several scenarios on the tiled path advance together, unless asked not to
+  bool batched = n_scen > 1 && !(o.flags & MBS_SOLVE_ONE_AT_A_TIME) && o.algo != MBS_ALGO_PLAIN &&
+                 o.check_every == 0;
+  for (int i = 0; i < n_scen && batched; ++i) batched = default_algo(batch[i], o.precision) == MBS_ALGO_TILED;
+  if (batched) {
+    std::vector<mbs_scenario_s *> ss(batch, batch + n_scen);
+    return solve_batch(ss, o, st);
+  }
+  for (int i = 0; i < n_scen; ++i) {
     const int rc = solve_one(batch[i], o, st);
     if (rc) return rc;
   }

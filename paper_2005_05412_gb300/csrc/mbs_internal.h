@@ -24,6 +24,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <vector_types.h>
 
 namespace mbs {
 
@@ -96,6 +97,10 @@ int set_error(int code, const char *msg);
 int launch_plain_step(const Args &a, long long n, int cur, void *stream);
 int launch_tiled(const Args &a, long long n0, int nsteps, int T, int cur, void *stream);
 int tiled_supported(int prec, int N);
+int tiled_variant(const Args &a);
+size_t tiled_batch_smem(int prec, int N, int max_mat_all, int max_slot, int max_qstride);
+int launch_tiled_batch(int prec, int N, int pm, const Args *args, const int2 *tasks, int n_tasks, size_t smem,
+                       long long n0, int T, int cur, void *stream);
 int launch_check(const Args &a, int cur, const int *cells, int n_cells, double *out_min_eig,
                  double *out_trace_dev, const void *zref_full, const void *V, void *stream);
 

@@ -26,4 +26,40 @@ int launch_tiled(const Args &a, long long n0, int nsteps, int T, int cur, void *
   return (int)cudaErrorInvalidValue;
 }
 
+// Kernel variant of a scenario for the tiled path: (N, PM) with PM as in
+// k_tiled; -1 if the tiled path does not cover it.
+int tiled_variant(const Args &a) {
+  if (a.N == 2) return a.pcell2 ? 2 : (a.pcell ? 1 : 0);
+  if (a.N == 3 && !a.pcell) return 0;
+  return -1;
+}
+
+size_t tiled_batch_smem(int prec, int N, int max_mat_all, int max_slot, int max_qstride) {
+  if (prec == 0)
+    return N == 2 ? tiled_smem<double, 2, 4>(max_mat_all, max_slot, max_qstride)
+                  : tiled_smem<double, 3, 2>(max_mat_all, max_slot, max_qstride);
+  return N == 2 ? tiled_smem<float, 2, 4>(max_mat_all, max_slot, max_qstride)
+                : tiled_smem<float, 3, 2>(max_mat_all, max_slot, max_qstride);
+}
+
+int launch_tiled_batch(int prec, int N, int pm, const Args *args, const int2 *tasks, int n_tasks, size_t smem,
+                       long long n0, int T, int cur, void *stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (N == 2) {
+    if (prec == 0) {
+      if (pm == 2) return tiled_batch_impl<double, 2, 4, false, 2>(args, tasks, n_tasks, smem, n0, T, cur, st);
+      if (pm == 1) return tiled_batch_impl<double, 2, 4, false, 1>(args, tasks, n_tasks, smem, n0, T, cur, st);
+      return tiled_batch_impl<double, 2, 4, false, 0>(args, tasks, n_tasks, smem, n0, T, cur, st);
+    }
+    if (pm == 2) return tiled_batch_impl<float, 2, 4, true, 2>(args, tasks, n_tasks, smem, n0, T, cur, st);
+    if (pm == 1) return tiled_batch_impl<float, 2, 4, true, 1>(args, tasks, n_tasks, smem, n0, T, cur, st);
+    return tiled_batch_impl<float, 2, 4, true, 0>(args, tasks, n_tasks, smem, n0, T, cur, st);
+  }
+  if (N == 3 && pm == 0) {
+    if (prec == 0) return tiled_batch_impl<double, 3, 2, false, 0>(args, tasks, n_tasks, smem, n0, T, cur, st);
+    return tiled_batch_impl<float, 3, 2, true, 0>(args, tasks, n_tasks, smem, n0, T, cur, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
 }  // namespace mbs
