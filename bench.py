@@ -220,6 +220,8 @@ def run_ours(args, rank, world, local):
            "wall_s": round(wall, 3)}
     if rank == 0 and not args.quick:
         out["fp64_plain"] = fp64_plain(p, mbs, stream, torch)
+        if not args.no_batch:
+            out["batch"] = batch_leg(mbs, stream, torch, args.precision, T)
         out["e2e"] = e2e(p, mbs, args, torch, stream)
         if world == 1 and not args.no_cpu:
             cb = time_oracle(p)
@@ -227,6 +229,33 @@ def run_ours(args, rank, world, local):
                                    "kind": "oracle", "sample": cb["sample"]}
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def batch_leg(mbs, stream, torch, precision, T):
+    """The 512-simulation mixed batch (two- and three-level media, 1,024 to
+    65,536 cells, 20,000 to 100,000 steps): one batched solve against the
+    same scenarios solved one after another."""
+    ps = W.batch_mixed()
+    devs = [mbs.device_from_problem(p) for p in ps]
+    scs = [mbs.scenario_from_problem(d, p) for d, p in zip(devs, ps)]
+    cell_steps = sum(p.n_cells * p.n_steps for p in ps)
+    out = {}
+    for mode in ("batched", "one_at_a_time"):
+        one = mode == "one_at_a_time"
+        if not one:
+            mbs.mbs_solve(scs, precision, "tiled", tile_steps=T, stream=stream.cuda_stream)   # warm-up
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mbs.mbs_solve(scs, precision, "tiled", tile_steps=T, stream=stream.cuda_stream, one_at_a_time=one)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[mode] = cell_steps / (a.elapsed_time(b) / 1e3) / 1e9
+    n2 = sum(1 for p in ps if p.qms[0].n_levels == 2)
+    return {"value": round(out["batched"], 2), "one_at_a_time": round(out["one_at_a_time"], 2),
+            "speedup": round(out["batched"] / out["one_at_a_time"], 2), "unit": METRIC,
+            "workload": f"{len(ps)} simulations ({n2} two-level, {len(ps) - n2} three-level), "
+                        f"{cell_steps:.3e} cell-steps", "precision": precision, "tile_steps": T}
 
 
 def fp64_plain(p, mbs, stream, torch, steps=4000):
@@ -325,6 +354,7 @@ def main():
     ap.add_argument("--tile", type=int, default=12)
     ap.add_argument("--quick", action="store_true", help="skip the FP64, e2e and CPU legs")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-simulation batch leg")
     ap.add_argument("--nsteps", type=int, default=0, help="override the workload's step count (profiling)")
     args = ap.parse_args()
     rank, world, local = dist_env()
