@@ -161,7 +161,7 @@ enum { MBS_SOLVE_ONE_AT_A_TIME = 1 };  /* flags: solve batch members one after a
 typedef struct {
     int precision;     /* MBS_PREC_* */
     int algo;          /* MBS_ALGO_* */
-    int tile_steps;    /* steps per tiled launch (multiple of 4), 0 = default (12) */
+    int tile_steps;    /* steps per tiled launch (multiple of 4), 0 = default (24 for two levels, 32 for three) */
     int check_every;   /* steps between device-side state checks, 0 = only at the end */
     int flags;         /* MBS_SOLVE_* */
 } mbs_opts;
@@ -170,9 +170,12 @@ typedef struct {
  * results are discarded).  `cuda_stream` is a cudaStream_t or NULL for the
  * legacy default stream.  The call returns after the work has completed.
  * Several scenarios on the tiled path (algo AUTO or TILED, check_every 0, no
- * MBS_SOLVE_ONE_AT_A_TIME) advance together: each round of tile_steps steps
- * is one launch per kernel variant over the blocks of all scenarios still
- * running (scenarios may differ in cells, levels, steps and parameters).
+ * MBS_SOLVE_ONE_AT_A_TIME) advance together, grouped by kernel variant (level
+ * count and parameter layout): each round of a group's tile_steps steps is
+ * one launch over the blocks of the group's scenarios still running
+ * (scenarios may differ in cells, steps and parameters).  With more than one
+ * group, each group runs on a stream forked from cuda_stream and joined back
+ * into it.
  * Returns MBS_E_NUMERIC if a state check found a non-finite value or a
  * density-matrix eigenvalue below -1e-6 (in a batch: the first such status,
  * after every member has finished). */

@@ -10,15 +10,16 @@
 //    records} -- with the kernel boundary as the paper's sync();
 //
 //  * tiled (the redundant-calculation loop of Sec. 3.2, re-designed for the
-//    GPU): each warp owns a segment of cells and advances it T steps per
+//    GPU): each block owns a segment of cells and advances it T steps per
 //    launch entirely in registers.  A lane holds R consecutive cells; the
-//    only neighbour traffic is one warp shuffle of E to the right and one of
-//    H to the left per step.  The warp loads its segment plus a T-cell halo
-//    on each side; the halo shrinks by one cell per side per step (the
-//    light cone of the 3-point stencil), so after T steps the owned cells
-//    are exact and are the only ones written back.  Ping-pong buffers keep
-//    neighbouring warps' halo reads race-free.  No shared-memory traffic or
-//    block barrier happens inside the time loop.
+//    neighbour traffic is one warp shuffle of E to the right and one of H to
+//    the left per step, plus the values at the block's inner warp edges,
+//    which pass through shared memory between two block barriers per step.
+//    The block loads its segment plus a T-cell halo on each side; the halo
+//    shrinks by one cell per side per step (the light cone of the 3-point
+//    stencil), so after T steps the owned cells are exact and are the only
+//    ones written back.  Ping-pong buffers keep neighbouring blocks' halo
+//    reads race-free.
 //
 // In FP32 the fields are float-float pairs (see "fields" below).
 // The field rotation needs sin(theta) and cos(theta) - 1 of small angles to
@@ -221,6 +222,113 @@ __device__ __forceinline__ void bloch_accumulate(const Prm &q, const real (&u)[N
         kahan_add(d[i], cc[i], acc);
       else
         d[i] += acc;
+    }
+  }
+}
+
+// bloch_step for the R cells of one lane that share one material block:
+// every parameter is read once and applied to all R cells (per cell, the
+// arithmetic and its order are those of bloch_step).  u[i][j] is cell j's
+// rotated deviation, pw[j] its coupling w . u + w0.
+// M contiguous values from a 16-byte aligned address, in 16-byte loads
+template <typename real, int M>
+__device__ __forceinline__ void ld_vec16(const real *p, real (&v)[M]) {
+  constexpr int W = 16 / sizeof(real);
+  static_assert(M % W == 0, "whole vectors only");
+#pragma unroll
+  for (int k = 0; k < M / W; ++k) {
+    if constexpr (sizeof(real) == 4) {
+      const float4 t = reinterpret_cast<const float4 *>(p)[k];
+      v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+    } else {
+      const double2 t = reinterpret_cast<const double2 *>(p)[k];
+      v[2 * k] = t.x; v[2 * k + 1] = t.y;
+    }
+  }
+}
+
+template <typename real, int N, int R, bool KAHAN>
+__device__ __forceinline__ void bloch_step_rows(const real *mb, const real (&e)[R], real (&d)[N * N - 1][R],
+                                                real (&cc)[N * N - 1][R], real (&u)[N * N - 1][R],
+                                                real (&pw)[R]) {
+  constexpr int K = N * N - 1, P = N * (N - 1) / 2, NP = N - 1;
+  static_assert(K <= 15, "rows are unrolled");
+  // With K a multiple of 4 every row of the block starts on a 16-byte
+  // boundary (the block stride is a multiple of 4 words), so the rows are
+  // read as vectors: tail = w0 | kap[P] | zr[2P], padded to whole vectors.
+  constexpr bool VEC = K % 4 == 0;
+  constexpr int TL = VEC ? (1 + 3 * P + 3) / 4 * 4 : 1;
+  const PrmBlock<real, N> q{mb};
+  real tail[TL];
+  if constexpr (VEC) ld_vec16<real, TL>(mb + K * K + 2 * K, tail);
+  auto w0 = [&]() { if constexpr (VEC) return tail[0]; else return q.w0(); };
+  auto kap = [&](int p) { if constexpr (VEC) return tail[1 + p]; else return q.kap(p); };
+  auto zr = [&](int i) { if constexpr (VEC) return tail[1 + P + i]; else return q.zr(i); };
+  real rx[2 * P][R];
+#pragma unroll
+  for (int i = 0; i < NP; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) u[i][j] = d[i][j];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const real kp = kap(p), za = zr(2 * p), zb = zr(2 * p + 1);
+    const int ia = NP + 2 * p, ib = ia + 1;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      real s, cm1;
+      sincos_m1(kp * e[j], s, cm1);
+      const real xa = za + d[ia][j];
+      const real xb = zb + d[ib][j];
+      const real ra = cm1 * xa - s * xb;
+      const real rb = s * xa + cm1 * xb;
+      rx[2 * p][j] = ra;
+      rx[2 * p + 1][j] = rb;
+      u[ia][j] = d[ia][j] + ra;
+      u[ib][j] = d[ib][j] + rb;
+    }
+  }
+  {
+    real wv[K];
+    if constexpr (VEC) ld_vec16<real, K>(mb + K * K + K, wv);
+    else
+#pragma unroll
+      for (int i = 0; i < K; ++i) wv[i] = q.w(i);
+    const real w00 = w0();
+#pragma unroll
+    for (int j = 0; j < R; ++j) pw[j] = w00;
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) pw[j] += wv[i] * u[i][j];
+  }
+  real cv[K];
+  if constexpr (VEC) ld_vec16<real, K>(mb + K * K, cv);
+  else
+#pragma unroll
+    for (int i = 0; i < K; ++i) cv[i] = q.c(i);
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    real row[K];
+    if constexpr (VEC) ld_vec16<real, K>(mb + i * K, row);
+    else
+#pragma unroll
+      for (int k = 0; k < K; ++k) row[k] = q.am1(i, k);
+    real acc[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      acc[j] = cv[i];
+      if (i >= NP) acc[j] += rx[i - NP][j];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int j = 0; j < R; ++j) acc[j] += row[k] * u[k][j];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      if (KAHAN)
+        kahan_add(d[i][j], cc[i][j], acc[j]);
+      else
+        d[i][j] += acc[j];
     }
   }
 }
@@ -545,9 +653,10 @@ __device__ __forceinline__ void st_row<double, 4>(double *p, const double (&v)[4
   reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
 }
 
-// Warp w owns cells [w*own, (w+1)*own), own = 32 R - 2 T; lane l holds cells
-// tb + l R .. tb + l R + R - 1 with tb = w*own - T.  Reads buffers `cur`,
-// writes the owned cells of buffers cur ^ 1.
+// Block tile b owns cells [b*own, (b+1)*own), own = 32 W R - 2 T (W warps);
+// lane l of warp w holds cells tb + (32 w + l) R .. + R - 1 with tb = b*own - T
+// (the tile holding the last cell may start 4 or 8 cells earlier).  Reads
+// buffers `cur`, writes the owned cells of buffers cur ^ 1.
 //   PM = 0: step operator of the lane's medium from shared memory;
 //   PM = 1: dense per-cell step operator rows in registers (jittered media);
 //   PM = 2: structured two-level per-cell rows in registers (see PrmBloch2).
@@ -555,7 +664,7 @@ __device__ __forceinline__ void st_row<double, 4>(double *p, const double (&v)[4
 // scheduler only inside one basic block, so vacuum cells run the Bloch step
 // with a zero field angle and a zero coupling instead of being skipped.
 template <typename real, int N, int R, bool KAHAN, int PM>
-__device__ __forceinline__ void tile_body(const Args &a, const int warp, long long n0, int nsteps, int T, int cur,
+__device__ __forceinline__ void tile_body(const Args &a, const int tile, long long n0, int nsteps, int T, int cur,
                                           unsigned char *smem_raw) {
   constexpr int K = N * N - 1;
   constexpr bool FF = sizeof(real) == 4;
@@ -568,24 +677,35 @@ __device__ __forceinline__ void tile_body(const Args &a, const int warp, long lo
   for (int i = threadIdx.x; i < a.n_slot * a.qstride; i += blockDim.x) s_q[i] = reinterpret_cast<const real *>(a.qpar)[i];
   for (int i = threadIdx.x; i < a.n_mat_all; i += blockDim.x) s_slot[i] = a.qslot[i];
   __syncthreads();
-  // this thread's slot for the rotated state of its probe cells
-  real *s_u = reinterpret_cast<real *>(reinterpret_cast<unsigned char *>(s_slot) +
-                                       ((sizeof(int) * a.n_mat_all + 15) / 16) * 16) +
-              (size_t)threadIdx.x * R * K;
+  // this thread's slot for the rotated state of its probe cells, then the
+  // warp-edge exchange slots [warp][E hi, E lo, H hi, H lo]
+  real *s_ub = reinterpret_cast<real *>(reinterpret_cast<unsigned char *>(s_slot) +
+                                        ((sizeof(int) * a.n_mat_all + 15) / 16) * 16);
+  real *s_u = s_ub + (size_t)threadIdx.x * R * K;
+  constexpr int TW = TileGeom<N>::W;            // warps per block
+  real *s_x = s_ub + (size_t)32 * TW * R * K;
 
-  const int lane = threadIdx.x & 31;
-  const int own = 32 * R - 2 * T;
-  int c_own = warp * own;
-  if (c_own >= a.nx) return;   // whole warp leaves together
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  constexpr int SPAN = 32 * R;                  // cells per warp
+  constexpr int TSPAN = TW * SPAN;              // cells per tile
+  const int own = TSPAN - 2 * T;
+  const int c_own = tile * own;
+  if (c_own >= a.nx) return;   // the whole block leaves together
   // The absorbing right end reads its neighbour's new E (first-order Mur), a
-  // dependency one cell beyond the stencil's light cone: that neighbour must
-  // be owned by the same warp.  If the last cell would start a warp's owned
-  // range, that warp starts 4 cells earlier; the 4 shared cells are valid in
-  // both warps and both write identical values.
-  if (warp > 0 && c_own == a.nx - 1) c_own -= 4;
-  const int tb = c_own - T;
-  const int g0 = tb + lane * R;         // first cell of this lane
-  const int base = a.off + g0;          // its array index (>= 0, multiple of R)
+  // dependency one cell beyond the stencil's light cone: the neighbour must
+  // stay valid for all T steps (so the last cell may not be the tile's first
+  // owned cell) and be held by the same warp (so the last cell may not start
+  // a warp).  The tile that owns the last cell starts 4 (or 8) cells earlier
+  // when either would happen; T <= 32 R - 12 keeps its owned cells inside.
+  int tb = c_own - T;
+  if (a.nx - 1 < c_own + own) {
+    if (a.nx - 1 == c_own || (a.nx - 1 - tb) % SPAN == 0) tb -= 4;
+    if ((a.nx - 1 - tb) % SPAN == 0) tb -= 4;
+  }
+  const int lo = c_own - tb;                    // tile position of the first owned cell
+  const int ti0 = wib * SPAN + lane * R;        // tile position of this lane's first cell
+  const int g0 = tb + ti0;                      // first cell of this lane
+  const int base = a.off + g0;                  // its array index (>= 0, multiple of R)
 
   real E[R], El[R], H[R], Hl[R];
   real d[K][R], cc[K][R];
@@ -660,29 +780,40 @@ __device__ __forceinline__ void tile_body(const Args &a, const int warp, long lo
     }
   }
   // warp-uniform: does the tile touch a source, a boundary cell, a probe?
-  const int t_lo = tb, t_hi = tb + 32 * R;   // [t_lo, t_hi)
+  const int t_lo = tb + wib * SPAN, t_hi = t_lo + SPAN;   // this warp's cells [t_lo, t_hi)
   bool any_src = false;
   for (int s = 0; s < a.n_src; ++s)
     any_src |= (a.src[s].cell >= t_lo && a.src[s].cell < t_hi) || (a.src[s].face >= t_lo && a.src[s].face < t_hi);
   const bool any_bnd = (t_lo <= 0 && 0 < t_hi) || (t_lo <= a.nx - 1 && a.nx - 1 < t_hi);
-  // probes owned by this lane
+  // owned cells of this lane (T, lo and own are multiples of R)
+  const bool owned = ti0 >= lo && ti0 < lo + own && ti0 < TSPAN - T;
   unsigned pmask = 0;
-  const int ti0 = lane * R;
   for (int p = 0; p < a.n_probe; ++p) {
     const int j = a.pr_cell[p] - g0;
-    if (j >= 0 && j < R && ti0 + j >= T && ti0 + j < 32 * R - T) pmask |= 1u << j;
+    if (owned && j >= 0 && j < R) pmask |= 1u << j;
   }
   const bool any_probe = __any_sync(FULL, pmask != 0);
   real *rec = reinterpret_cast<real *>(a.rec);
   const real *pcoef = reinterpret_cast<const real *>(a.pr_coef);
+
+  // E of each warp's last cell, for the next warp's first face
+  if (lane == 31) {
+    s_x[wib * 4 + 0] = E[R - 1];
+    s_x[wib * 4 + 1] = El[R - 1];
+  }
+  __syncthreads();
 
 #pragma unroll 1
   for (int t = 0; t < nsteps; ++t) {
     const long long n = n0 + t;
     // ---- H^{n+1/2} on the left faces of my cells (in place)
     {
-      const real elh = __shfl_up_sync(FULL, E[R - 1], 1);
-      const real ell = FF ? __shfl_up_sync(FULL, El[R - 1], 1) : real(0);
+      real elh = __shfl_up_sync(FULL, E[R - 1], 1);
+      real ell = FF ? __shfl_up_sync(FULL, El[R - 1], 1) : real(0);
+      if (lane == 0 && wib > 0) {
+        elh = s_x[(wib - 1) * 4 + 0];
+        ell = s_x[(wib - 1) * 4 + 1];
+      }
 #pragma unroll
       for (int j = R - 1; j >= 0; --j)
         fld_axpy_diff<real, true>(H[j], Hl[j], ch[j], E[j], El[j], j ? E[j - 1] : elh, j ? El[j - 1] : ell, real(0));
@@ -699,12 +830,29 @@ __device__ __forceinline__ void tile_body(const Args &a, const int warp, long lo
           }
       }
     }
+    // H of each warp's first face, for the previous warp's last cell
+    if (lane == 0) {
+      s_x[wib * 4 + 2] = H[0];
+      s_x[wib * 4 + 3] = Hl[0];
+    }
     // ---- rho^{n+1/2} and the coupling term (all cells of a warp that holds
     // any medium; vacuum cells see a zero angle and contribute no current)
     real pw[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) pw[j] = real(0);
-    if (warp_med) {
+    if (warp_med && PM == 0) {
+      real ej[R], u[K][R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) ej[j] = fld_val<real>(E[j], El[j]) * mk[j];
+      bloch_step_rows<real, N, R, KAHAN>(mb, ej, d, cc, u, pw);
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        pw[j] *= mk[j];
+        if (pmask & (1u << j))   // park u of probe cells (predicated stores)
+#pragma unroll
+          for (int i = 0; i < K; ++i) s_u[j * K + i] = u[i][j];
+      }
+    } else if (warp_med) {
 #pragma unroll
       for (int j = 0; j < R; ++j) {
         real dj[K], cj[K], u[K];
@@ -717,10 +865,8 @@ __device__ __forceinline__ void tile_body(const Args &a, const int warp, long lo
         real q;
         if constexpr (PM == 2)
           q = bloch_step_b2<real, KAHAN>(b2[j], ej, dj, cj, u);
-        else if constexpr (PM == 1)
-          q = bloch_step<real, N, KAHAN>(pr[PERCELL ? j : 0], ej, dj, cj, u);
         else
-          q = bloch_step<real, N, KAHAN>(PrmBlock<real, N>{mb}, ej, dj, cj, u);
+          q = bloch_step<real, N, KAHAN>(pr[PERCELL ? j : 0], ej, dj, cj, u);
         pw[j] = q * mk[j];
 #pragma unroll
         for (int i = 0; i < K; ++i) {
@@ -731,6 +877,8 @@ __device__ __forceinline__ void tile_body(const Args &a, const int warp, long lo
 #pragma unroll
           for (int i = 0; i < K; ++i) s_u[j * K + i] = u[i];
       }
+    }
+    if (warp_med) {
       if (any_probe && pmask) {
 #pragma unroll
         for (int j = 0; j < R; ++j)
@@ -765,10 +913,15 @@ __device__ __forceinline__ void tile_body(const Args &a, const int warp, long lo
         }
       }
     }
+    __syncthreads();   // H of the warp edges published
     // ---- E^{n+1} (in place)
     {
-      const real hrh = __shfl_down_sync(FULL, H[0], 1);
-      const real hrl = FF ? __shfl_down_sync(FULL, Hl[0], 1) : real(0);
+      real hrh = __shfl_down_sync(FULL, H[0], 1);
+      real hrl = FF ? __shfl_down_sync(FULL, Hl[0], 1) : real(0);
+      if (lane == 31 && wib < TW - 1) {
+        hrh = s_x[(wib + 1) * 4 + 2];
+        hrl = s_x[(wib + 1) * 4 + 3];
+      }
 #pragma unroll
       for (int j = 0; j < R; ++j)
         fld_axpy_diff<real, true>(E[j], El[j], cb[j], j < R - 1 ? H[j + 1] : hrh, j < R - 1 ? Hl[j + 1] : hrl, H[j],
@@ -827,10 +980,14 @@ __device__ __forceinline__ void tile_body(const Args &a, const int warp, long lo
             if (a.pr_cell[p] == g0 + j && a.pr_q[p] < 2)
               rec[(size_t)p * a.nt + n] = a.pr_q[p] == 0 ? fld_val<real>(E[j], El[j]) : fld_val<real>(H[j], Hl[j]);
     }
+    if (lane == 31) {
+      s_x[wib * 4 + 0] = E[R - 1];
+      s_x[wib * 4 + 1] = El[R - 1];
+    }
+    __syncthreads();   // E of the warp edges published
   }
 
   // ---- write back the owned cells (never past the last cell)
-  const bool owned = ti0 >= T && ti0 < 32 * R - T;   // T is a multiple of R
   if (!owned) return;
   if constexpr (FF) {
 #pragma unroll
@@ -876,26 +1033,31 @@ __device__ __forceinline__ void tile_body(const Args &a, const int warp, long lo
   }
 }
 
-// One simulation: warp w of the grid is warp w of the simulation.
+// Blocks that must fit on one SM at a time (caps the registers): the FP32
+// kernels run fastest with 2 (three levels, 8 warps) or 4 (two levels, 4
+// warps, shared or structured rows) resident blocks (measured).
+template <typename real, int N, int PM>
+constexpr int tiled_min_blocks() { return sizeof(real) != 4 ? 1 : N == 3 ? 2 : PM != 1 ? 4 : 1; }
+
+// One simulation: block b advances tile b.
 template <typename real, int N, int R, bool KAHAN, int PM>
-__global__ void __launch_bounds__(128) k_tiled(const __grid_constant__ Args a, long long n0, int nsteps, int T, int cur) {
+__global__ void __launch_bounds__(32 * TileGeom<N>::W, tiled_min_blocks<real, N, PM>()) k_tiled(const __grid_constant__ Args a, long long n0, int nsteps, int T, int cur) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  tile_body<real, N, R, KAHAN, PM>(a, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, n0, nsteps, T, cur, smem_raw);
+  tile_body<real, N, R, KAHAN, PM>(a, blockIdx.x, n0, nsteps, T, cur, smem_raw);
 }
 
-// A batch of simulations in one launch: block b works for simulation
-// tasks[b].x, starting at that simulation's warp tasks[b].y (all warps of a
-// block belong to one simulation).  Every simulation starts at step 0, so
+// A batch of simulations in one launch: block b advances tile tasks[b].y of
+// simulation tasks[b].x.  Every simulation starts at step 0, so
 // step n0 is common; finished simulations return at once.
 template <typename real, int N, int R, bool KAHAN, int PM>
-__global__ void __launch_bounds__(128) k_tiled_batch(const Args *__restrict__ args, const int2 *__restrict__ tasks,
+__global__ void __launch_bounds__(32 * TileGeom<N>::W, tiled_min_blocks<real, N, PM>()) k_tiled_batch(const Args *__restrict__ args, const int2 *__restrict__ tasks,
                                                      long long n0, int T, int cur) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int2 tk = tasks[blockIdx.x];
   const Args &a = args[tk.x];
   if (n0 >= a.nt) return;   // the whole block leaves together
   const int nsteps = (int)(a.nt - n0 < (long long)T ? a.nt - n0 : (long long)T);
-  tile_body<real, N, R, KAHAN, PM>(a, tk.y + (int)(threadIdx.x >> 5), n0, nsteps, T, cur, smem_raw);
+  tile_body<real, N, R, KAHAN, PM>(a, tk.y, n0, nsteps, T, cur, smem_raw);
 }
 
 
@@ -1029,17 +1191,17 @@ int plain_step_impl(const Args &a, long long n, int cur, cudaStream_t st) {
 template <typename real, int N, int R>
 size_t tiled_smem(int n_mat_all, int n_slot, int qstride) {
   return sizeof(real) * (n_mat_all * 4 + n_slot * qstride) + ((sizeof(int) * n_mat_all + 15) / 16) * 16 +
-         sizeof(real) * (size_t)128 * R * (N * N - 1) + 16;
+         sizeof(real) * ((size_t)32 * TileGeom<N>::W * R * (N * N - 1) + 4 * TileGeom<N>::W) + 16;
 }
 
 template <typename real, int N, int R, bool KAHAN, int PM>
 int tiled_impl(const Args &a, long long n0, int nsteps, int T, int cur, cudaStream_t st) {
-  const int own = 32 * R - 2 * T;
-  const int n_warps = (a.nx + own - 1) / own;
-  const int bs = 128, wpb = bs / 32;
-  const int gs = (n_warps + wpb - 1) / wpb;
+  constexpr int TW = TileGeom<N>::W;
+  static_assert(32 * TW * R - 5 <= PAD, "a tile reaches past the pad cells");
+  const int own = 32 * TW * R - 2 * T;
+  const int gs = (a.nx + own - 1) / own;
   const size_t sm = tiled_smem<real, N, R>(a.n_mat_all, a.n_slot, a.qstride);
-  k_tiled<real, N, R, KAHAN, PM><<<gs, bs, sm, st>>>(a, n0, nsteps, T, cur);
+  k_tiled<real, N, R, KAHAN, PM><<<gs, 32 * TW, sm, st>>>(a, n0, nsteps, T, cur);
   return (int)cudaGetLastError();
 }
 
@@ -1047,7 +1209,7 @@ template <typename real, int N, int R, bool KAHAN, int PM>
 int tiled_batch_impl(const Args *args, const int2 *tasks, int n_tasks, size_t smem, long long n0, int T, int cur,
                      cudaStream_t st) {
   if (n_tasks <= 0) return 0;
-  k_tiled_batch<real, N, R, KAHAN, PM><<<n_tasks, 128, smem, st>>>(args, tasks, n0, T, cur);
+  k_tiled_batch<real, N, R, KAHAN, PM><<<n_tasks, 32 * TileGeom<N>::W, smem, st>>>(args, tasks, n0, T, cur);
   return (int)cudaGetLastError();
 }
 

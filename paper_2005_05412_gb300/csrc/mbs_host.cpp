@@ -1180,6 +1180,10 @@ static int prepare_solve(mbs_scenario_s *s, int prec, cudaStream_t st) {
   return MBS_OK;
 }
 
+// Tile depth when the caller leaves it to the library: the fastest measured
+// on GB300 (two levels: 24 steps, three levels: 32).
+static int default_tile_steps(int N) { return N == 2 ? 24 : 32; }
+
 static int default_algo(const mbs_scenario_s *s, int prec) {
   return mbs::tiled_supported(prec, s->N) && (!s->has_pcell || s->N == 2) ? MBS_ALGO_TILED : MBS_ALGO_PLAIN;
 }
@@ -1188,9 +1192,9 @@ static int default_algo(const mbs_scenario_s *s, int prec) {
 static int tiled_ok(const mbs_scenario_s *s, int prec, int T) {
   if (!mbs::tiled_supported(prec, s->N) || (s->has_pcell && s->N != 2))
     return fail(MBS_E_INVALID, "tiled kernels cover N = 2 (also with per-cell factors) and N = 3");
-  const int R = s->N == 2 ? 4 : 2;
-  if (T % 4 != 0 || T < 4 || 32 * R - 2 * T < 8)
-    return fail(MBS_E_INVALID, "tile_steps must be a multiple of 4 in [4, %d]", (32 * R - 8) / 2);
+  const int R = mbs::tile_lane_cells(s->N);
+  if (T % 4 != 0 || T < 4 || T > mbs::tile_max_steps(s->N))
+    return fail(MBS_E_INVALID, "tile_steps must be a multiple of 4 in [4, %d]", mbs::tile_max_steps(s->N) / 4 * 4);
   // each lane's R-cell group must hold at most one medium material
   for (int g = 0; g * R < s->dev->nx; ++g) {
     int sl = -1;
@@ -1247,7 +1251,7 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
   if (rc) return rc;
   mbs::Args a = make_args(s, prec);
   int algo = o.algo == MBS_ALGO_AUTO ? default_algo(s, prec) : o.algo;
-  const int T = o.tile_steps > 0 ? o.tile_steps : 12;
+  const int T = o.tile_steps > 0 ? o.tile_steps : default_tile_steps(s->N);
   const int chk = o.check_every > 0 ? o.check_every : 0;
   int cur = 0;
   if (algo == MBS_ALGO_TILED) {
@@ -1287,14 +1291,13 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
 // the running ones form a prefix and the grid shrinks as simulations end.
 static int solve_batch(std::vector<mbs_scenario_s *> &ss, const mbs_opts &o, cudaStream_t st) {
   const int prec = o.precision;
-  const int T = o.tile_steps > 0 ? o.tile_steps : 12;
   int rc;
   for (auto *s : ss) {
     if ((rc = prepare_solve(s, prec, st))) return rc;
-    if ((rc = tiled_ok(s, prec, T))) return rc;
+    if ((rc = tiled_ok(s, prec, o.tile_steps > 0 ? o.tile_steps : default_tile_steps(s->N)))) return rc;
   }
   struct Group {
-    int N, pm;
+    int N, pm, T;
     std::vector<int> sims;        // indices into ss, longest first
     std::vector<int2> tasks;
     std::vector<long long> task_nt;
@@ -1310,7 +1313,7 @@ static int solve_batch(std::vector<mbs_scenario_s *> &ss, const mbs_opts &o, cud
     for (auto &x : groups)
       if (x.N == ss[i]->N && x.pm == pm) g = &x;
     if (!g) {
-      groups.push_back(Group{ss[i]->N, pm});
+      groups.push_back(Group{ss[i]->N, pm, o.tile_steps > 0 ? o.tile_steps : default_tile_steps(ss[i]->N)});
       g = &groups.back();
     }
     g->sims.push_back((int)i);
@@ -1320,10 +1323,10 @@ static int solve_batch(std::vector<mbs_scenario_s *> &ss, const mbs_opts &o, cud
   }
   for (auto &g : groups) {
     std::stable_sort(g.sims.begin(), g.sims.end(), [&](int x, int y) { return ss[x]->nt > ss[y]->nt; });
-    const int R = g.N == 2 ? 4 : 2, own = 32 * R - 2 * T;
+    const int own = mbs::tile_own(g.N, g.T);
     for (int i : g.sims) {
-      const int n_warps = (ss[i]->dev->nx + own - 1) / own;
-      for (int w = 0; w < n_warps; w += 4) {
+      const int n_tiles = (ss[i]->dev->nx + own - 1) / own;
+      for (int w = 0; w < n_tiles; ++w) {
         g.tasks.push_back(make_int2(i, w));
         g.task_nt.push_back(ss[i]->nt);
       }
@@ -1348,42 +1351,84 @@ static int solve_batch(std::vector<mbs_scenario_s *> &ss, const mbs_opts &o, cud
     cleanup();
     return cuda_fail(e, "batch tables");
   }
-  long long nt_max = 0;
-  for (auto *s : ss) nt_max = std::max(nt_max, s->nt);
-  int cur = 0;
-  for (long long n0 = 0; n0 < nt_max; n0 += T) {
-    for (size_t k = 0; k < groups.size(); ++k) {
-      const auto &g = groups[k];
+  // Each group runs on a stream of its own, forked from and joined back into
+  // the caller's stream, so that one group's last, thinly populated rounds
+  // overlap the other group's work.
+  const size_t n_fork = groups.size() > 1 ? groups.size() : 0;
+  std::vector<cudaStream_t> gst(groups.size(), st);
+  std::vector<cudaEvent_t> ev(n_fork + 1, nullptr);
+  auto release = [&]() {
+    for (size_t k = 0; k < n_fork; ++k)
+      if (gst[k] != st) cudaStreamDestroy(gst[k]);
+    for (auto x : ev)
+      if (x) cudaEventDestroy(x);
+  };
+  for (size_t k = 0; k < n_fork && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&gst[k], cudaStreamNonBlocking);
+    if (e != cudaSuccess) gst[k] = st;
+  }
+  for (size_t k = 0; k < ev.size() && n_fork && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+  if (n_fork && e == cudaSuccess) e = cudaEventRecord(ev[n_fork], st);
+  for (size_t k = 0; k < n_fork && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(gst[k], ev[n_fork], 0);
+  if (e != cudaSuccess) {
+    release();
+    cleanup();
+    return cuda_fail(e, "batch streams");
+  }
+  for (size_t k = 0; k < groups.size(); ++k) {
+    const auto &g = groups[k];
+    const size_t smem = mbs::tiled_batch_smem(prec, g.N, g.max_mat, g.max_slot, g.max_stride);
+    const long long nt_max = g.task_nt.front();
+    int cur = 0;
+    for (long long n0 = 0; n0 < nt_max; n0 += g.T) {
       // running blocks: a prefix of the tasks (sorted by step count)
       const int active = (int)(std::upper_bound(g.task_nt.begin(), g.task_nt.end(), n0,
                                                 [](long long v, long long x) { return v > x; }) -
                                g.task_nt.begin());
-      if (!active) continue;
-      const size_t smem = mbs::tiled_batch_smem(prec, g.N, g.max_mat, g.max_slot, g.max_stride);
-      const int r = mbs::launch_tiled_batch(prec, g.N, g.pm, d_args, d_tasks[k], active, smem, n0, T, cur, st);
+      const int r =
+          mbs::launch_tiled_batch(prec, g.N, g.pm, d_args, d_tasks[k], active, smem, n0, g.T, cur, gst[k]);
       if (r) {
+        release();
         cleanup();
         return cuda_fail((cudaError_t)r, "batched tiled launch");
       }
+      cur ^= 1;
     }
-    cur ^= 1;
+  }
+  for (size_t k = 0; k < n_fork && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(ev[k], gst[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[k], 0);
+  }
+  if (e != cudaSuccess) {
+    release();
+    cleanup();
+    return cuda_fail(e, "batch streams");
   }
   // final state check of every simulation in its own final buffer
+  std::vector<int> sim_T(ss.size());
+  for (const auto &g : groups)
+    for (int i : g.sims) sim_T[i] = g.T;
   for (size_t i = 0; i < ss.size(); ++i) {
     auto *s = ss[i];
+    const int T = sim_T[i];
     const long long rounds = (s->nt + T - 1) / T;
     s->launches = rounds;
     if ((rc = launch_state_check(s, args[i], (int)(rounds % 2), st))) {
+      cudaStreamSynchronize(st);
+      release();
       cleanup();
       return cuda_fail((cudaError_t)rc, "check launch");
     }
   }
   e = cudaStreamSynchronize(st);
+  release();
   cleanup();
   if (e != cudaSuccess) return cuda_fail(e, "batched solve");
   int status = MBS_OK;
-  for (auto *s : ss) {
-    const long long rounds = (s->nt + T - 1) / T;
+  for (size_t i = 0; i < ss.size(); ++i) {
+    auto *s = ss[i];
+    const long long rounds = (s->nt + sim_T[i] - 1) / sim_T[i];
     rc = finish_solve(s, prec, (int)(rounds % 2));
     if (rc && status == MBS_OK) status = rc;
   }

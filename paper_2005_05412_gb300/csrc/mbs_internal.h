@@ -31,7 +31,22 @@ namespace mbs {
 constexpr int NMAX = 6;
 constexpr int MAXSRC = 4;
 constexpr int MAXPROBE = 64;
-constexpr int PAD = 256;  // left/right margin cells of every cell array
+constexpr int PAD = 512;  // left/right margin cells of every cell array
+
+// Tiled kernel geometry per level count (the fastest measured on GB300): a
+// block of W warps advances one contiguous tile of 32 W R cells (R cells per
+// lane) by T steps and owns the tile minus a T-cell halo on each side.
+// T <= 32 R - 12 leaves room for the shift of the tile that holds the
+// absorbing right end (at most 8 cells).
+template <int N>
+struct TileGeom {
+  static constexpr int R = N == 2 ? 4 : 2;
+  static constexpr int W = N == 2 ? 4 : 8;
+};
+inline int tile_lane_cells(int N) { return N == 2 ? TileGeom<2>::R : TileGeom<3>::R; }
+inline int tile_warps(int N) { return N == 2 ? TileGeom<2>::W : TileGeom<3>::W; }
+inline int tile_own(int N, int T) { return 32 * tile_warps(N) * tile_lane_cells(N) - 2 * T; }
+inline int tile_max_steps(int N) { return 32 * tile_lane_cells(N) - 12; }
 
 // Packed per-quantum-material parameter block (in the state's real type):
 //   am1[K*K] (A - I, row-major) | c[K] | w[K] | w0 | kap[P] | zr[2P]
@@ -40,7 +55,7 @@ inline int q_k(int N) { return N * N - 1; }
 inline int q_p(int N) { return N * (N - 1) / 2; }
 inline int q_stride(int N) {
   int K = q_k(N), P = q_p(N);
-  return K * K + 2 * K + 1 + 3 * P;
+  return (K * K + 2 * K + 1 + 3 * P + 3) / 4 * 4;   // 16-byte multiple in FP32 (rows load as vectors)
 }
 // Per-cell parameter rows (cells with their own propagator): am1, c, w, w0.
 inline int pc_rows(int N) {

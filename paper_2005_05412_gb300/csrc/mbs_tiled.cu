@@ -4,6 +4,7 @@
 namespace mbs {
 using namespace dev;
 
+
 int tiled_supported(int prec, int N) { return (N == 2 || N == 3) && (prec == 0 || prec == 1); }
 
 int launch_tiled(const Args &a, long long n0, int nsteps, int T, int cur, void *stream) {
@@ -11,17 +12,17 @@ int launch_tiled(const Args &a, long long n0, int nsteps, int T, int cur, void *
   const bool pc = a.pcell != nullptr, b2 = a.pcell2 != nullptr;
   if (a.N == 2) {
     if (a.prec == 0) {
-      if (b2) return tiled_impl<double, 2, 4, false, 2>(a, n0, nsteps, T, cur, st);
-      return pc ? tiled_impl<double, 2, 4, false, 1>(a, n0, nsteps, T, cur, st)
-                : tiled_impl<double, 2, 4, false, 0>(a, n0, nsteps, T, cur, st);
+      if (b2) return tiled_impl<double, 2, TileGeom<2>::R, false, 2>(a, n0, nsteps, T, cur, st);
+      return pc ? tiled_impl<double, 2, TileGeom<2>::R, false, 1>(a, n0, nsteps, T, cur, st)
+                : tiled_impl<double, 2, TileGeom<2>::R, false, 0>(a, n0, nsteps, T, cur, st);
     }
-    if (b2) return tiled_impl<float, 2, 4, true, 2>(a, n0, nsteps, T, cur, st);
-    return pc ? tiled_impl<float, 2, 4, true, 1>(a, n0, nsteps, T, cur, st)
-              : tiled_impl<float, 2, 4, true, 0>(a, n0, nsteps, T, cur, st);
+    if (b2) return tiled_impl<float, 2, TileGeom<2>::R, true, 2>(a, n0, nsteps, T, cur, st);
+    return pc ? tiled_impl<float, 2, TileGeom<2>::R, true, 1>(a, n0, nsteps, T, cur, st)
+              : tiled_impl<float, 2, TileGeom<2>::R, true, 0>(a, n0, nsteps, T, cur, st);
   }
   if (a.N == 3 && !pc) {
-    if (a.prec == 0) return tiled_impl<double, 3, 2, false, 0>(a, n0, nsteps, T, cur, st);
-    return tiled_impl<float, 3, 2, true, 0>(a, n0, nsteps, T, cur, st);
+    if (a.prec == 0) return tiled_impl<double, 3, TileGeom<3>::R, false, 0>(a, n0, nsteps, T, cur, st);
+    return tiled_impl<float, 3, TileGeom<3>::R, true, 0>(a, n0, nsteps, T, cur, st);
   }
   return (int)cudaErrorInvalidValue;
 }
@@ -36,10 +37,10 @@ int tiled_variant(const Args &a) {
 
 size_t tiled_batch_smem(int prec, int N, int max_mat_all, int max_slot, int max_qstride) {
   if (prec == 0)
-    return N == 2 ? tiled_smem<double, 2, 4>(max_mat_all, max_slot, max_qstride)
-                  : tiled_smem<double, 3, 2>(max_mat_all, max_slot, max_qstride);
-  return N == 2 ? tiled_smem<float, 2, 4>(max_mat_all, max_slot, max_qstride)
-                : tiled_smem<float, 3, 2>(max_mat_all, max_slot, max_qstride);
+    return N == 2 ? tiled_smem<double, 2, TileGeom<2>::R>(max_mat_all, max_slot, max_qstride)
+                  : tiled_smem<double, 3, TileGeom<3>::R>(max_mat_all, max_slot, max_qstride);
+  return N == 2 ? tiled_smem<float, 2, TileGeom<2>::R>(max_mat_all, max_slot, max_qstride)
+                : tiled_smem<float, 3, TileGeom<3>::R>(max_mat_all, max_slot, max_qstride);
 }
 
 int launch_tiled_batch(int prec, int N, int pm, const Args *args, const int2 *tasks, int n_tasks, size_t smem,
@@ -47,17 +48,17 @@ int launch_tiled_batch(int prec, int N, int pm, const Args *args, const int2 *ta
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (N == 2) {
     if (prec == 0) {
-      if (pm == 2) return tiled_batch_impl<double, 2, 4, false, 2>(args, tasks, n_tasks, smem, n0, T, cur, st);
-      if (pm == 1) return tiled_batch_impl<double, 2, 4, false, 1>(args, tasks, n_tasks, smem, n0, T, cur, st);
-      return tiled_batch_impl<double, 2, 4, false, 0>(args, tasks, n_tasks, smem, n0, T, cur, st);
+      if (pm == 2) return tiled_batch_impl<double, 2, TileGeom<2>::R, false, 2>(args, tasks, n_tasks, smem, n0, T, cur, st);
+      if (pm == 1) return tiled_batch_impl<double, 2, TileGeom<2>::R, false, 1>(args, tasks, n_tasks, smem, n0, T, cur, st);
+      return tiled_batch_impl<double, 2, TileGeom<2>::R, false, 0>(args, tasks, n_tasks, smem, n0, T, cur, st);
     }
-    if (pm == 2) return tiled_batch_impl<float, 2, 4, true, 2>(args, tasks, n_tasks, smem, n0, T, cur, st);
-    if (pm == 1) return tiled_batch_impl<float, 2, 4, true, 1>(args, tasks, n_tasks, smem, n0, T, cur, st);
-    return tiled_batch_impl<float, 2, 4, true, 0>(args, tasks, n_tasks, smem, n0, T, cur, st);
+    if (pm == 2) return tiled_batch_impl<float, 2, TileGeom<2>::R, true, 2>(args, tasks, n_tasks, smem, n0, T, cur, st);
+    if (pm == 1) return tiled_batch_impl<float, 2, TileGeom<2>::R, true, 1>(args, tasks, n_tasks, smem, n0, T, cur, st);
+    return tiled_batch_impl<float, 2, TileGeom<2>::R, true, 0>(args, tasks, n_tasks, smem, n0, T, cur, st);
   }
   if (N == 3 && pm == 0) {
-    if (prec == 0) return tiled_batch_impl<double, 3, 2, false, 0>(args, tasks, n_tasks, smem, n0, T, cur, st);
-    return tiled_batch_impl<float, 3, 2, true, 0>(args, tasks, n_tasks, smem, n0, T, cur, st);
+    if (prec == 0) return tiled_batch_impl<double, 3, TileGeom<3>::R, false, 0>(args, tasks, n_tasks, smem, n0, T, cur, st);
+    return tiled_batch_impl<float, 3, TileGeom<3>::R, true, 0>(args, tasks, n_tasks, smem, n0, T, cur, st);
   }
   return (int)cudaErrorInvalidValue;
 }
