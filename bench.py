@@ -202,13 +202,24 @@ def run_ours(args, rank, world, local):
     per_launch_s = t_local / args.steps / max(1, launches)
     units_per_launch = p.n_cells * T
     achieved = alg_bytes * units_per_launch / per_launch_s / 1e9
-    traffic = load_traffic(args)
+    prof = load_profile(args)
+    traffic = prof.get("dram_bytes") if prof else None
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm or HBM_FALLBACK, "unit": "GB/s",
             "frac": round(achieved / (hbm or HBM_FALLBACK), 4), "traffic": traffic,
             "peak_source": "measured" if hbm else "fallback",
+            "binding": "instruction issue (temporal tiles keep the state on chip; see issue)",
             "kernel": f"k_tiled<{args.precision},N=2,percell> T={T}",
             "alg_bytes_per_cell_step": alg_bytes, "launch_ms": round(per_launch_s * 1e3, 5),
             "launches_per_solve": launches, "tiled_launches_per_solve": tiled_launches}
+    clocks = clk.summary()
+    if prof and prof.get("warp_inst") and clocks.get("sm_mhz"):
+        # warp instructions issued per second against the SM's issue limit
+        # (4 schedulers x 1 instruction per clock x 152 SMs at the sampled clock)
+        ach = prof["warp_inst"] / per_launch_s / 1e9
+        pk_i = 4 * 152 * clocks["sm_mhz"] / 1e3
+        roof["issue"] = {"achieved": round(ach, 1), "peak": round(pk_i, 1), "unit": "Gwarp-inst/s",
+                         "frac": round(ach / pk_i, 4), "warp_inst_per_launch": prof["warp_inst"],
+                         "source": "ncu smsp__inst_executed.sum of the same kernel and tile depth"}
     out = {"metric": METRIC, "value": round(value, 3), "unit": METRIC, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_max * 1e3 / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
@@ -216,12 +227,12 @@ def run_ours(args, rank, world, local):
            "config": {"workload": f"{p.name}: {p.n_cells} cells x {p.n_steps} steps, N=2, per-cell jitter",
                       "precision": args.precision, "algo": "tiled", "tile_steps": T,
                       "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)"},
-           "roofline": roof, "clocks": clk.summary(), "gpu_launches": launches * args.steps,
+           "roofline": roof, "clocks": clocks, "gpu_launches": launches * args.steps,
            "wall_s": round(wall, 3)}
     if rank == 0 and not args.quick:
         out["fp64_plain"] = fp64_plain(p, mbs, stream, torch)
         if not args.no_batch:
-            out["batch"] = batch_leg(mbs, stream, torch, args.precision, T)
+            out["batch"] = batch_leg(mbs, stream, torch, args.precision)
         out["e2e"] = e2e(p, mbs, args, torch, stream)
         if world == 1 and not args.no_cpu:
             cb = time_oracle(p)
@@ -231,10 +242,11 @@ def run_ours(args, rank, world, local):
         print(json.dumps(out), flush=True)
 
 
-def batch_leg(mbs, stream, torch, precision, T):
+def batch_leg(mbs, stream, torch, precision, T=0):
     """The 512-simulation mixed batch (two- and three-level media, 1,024 to
     65,536 cells, 20,000 to 100,000 steps): one batched solve against the
-    same scenarios solved one after another."""
+    same scenarios solved one after another (tile depth: the library's
+    default per level count unless T is given)."""
     ps = W.batch_mixed()
     devs = [mbs.device_from_problem(p) for p in ps]
     scs = [mbs.scenario_from_problem(d, p) for d, p in zip(devs, ps)]
@@ -255,7 +267,8 @@ def batch_leg(mbs, stream, torch, precision, T):
     return {"value": round(out["batched"], 2), "one_at_a_time": round(out["one_at_a_time"], 2),
             "speedup": round(out["batched"] / out["one_at_a_time"], 2), "unit": METRIC,
             "workload": f"{len(ps)} simulations ({n2} two-level, {len(ps) - n2} three-level), "
-                        f"{cell_steps:.3e} cell-steps", "precision": precision, "tile_steps": T}
+                        f"{cell_steps:.3e} cell-steps", "precision": precision,
+            "tile_steps": T if T else "library default (24 two-level, 32 three-level)"}
 
 
 def fp64_plain(p, mbs, stream, torch, steps=4000):
@@ -301,16 +314,19 @@ def e2e(p, mbs, args, torch, stream, reps=2):
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "seconds_per_step": round(t, 3)}
 
 
-def load_traffic(args):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary (profiles/traffic.json), or None when the kernel source changed
-    after the capture (the file records a hash of the source it measured)."""
+def load_profile(args):
+    """ncu figures per launch of the dominant kernel (DRAM bytes, warp
+    instructions) from the committed summary profiles/traffic.json, or None
+    when the kernel source changed after the capture (the file records a hash
+    of the source it measured) or no capture exists for this tile depth."""
     import hashlib
     f = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(f))
-        src = open(os.path.join(ROOT, d["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != d["kernel_source_sha256_16"]:
+        h = hashlib.sha256()
+        for name in d["sources"]:
+            h.update(open(os.path.join(ROOT, name), "rb").read())
+        if h.hexdigest()[:16] != d["kernel_source_sha256_16"]:
             return None
         return d.get(f"{args.precision}_T{args.tile}")
     except Exception:
@@ -351,7 +367,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sit_2lvl_jitter")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--tile", type=int, default=12)
+    ap.add_argument("--tile", type=int, default=24)
     ap.add_argument("--quick", action="store_true", help="skip the FP64, e2e and CPU legs")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-simulation batch leg")
