@@ -292,10 +292,12 @@ def scenario_from_problem(dev: Device, p, courant=None) -> Scenario:
 
 
 def run(p, precision="fp32", algo="auto", tile_steps=0, check_every=0, stream=None):
-    """Create, solve and fetch one problem; returns dict(records, dt, nt, stats)."""
+    """Create, solve and fetch one problem; returns dict(records, dt, nt,
+    stats, counters, device_status)."""
     dev = device_from_problem(p)
     sc = scenario_from_problem(dev, p)
     mbs_solve([sc], precision, algo, tile_steps, check_every, stream)
     dt, dz, nt = mbs_scenario_info(sc)
     rec = np.stack([mbs_fetch_records(sc, k) for k in range(len(p.probes))]) if p.probes else np.zeros((0, nt))
-    return dict(records=rec, dt=dt, nt=nt, stats=mbs_scenario_stats(sc), device_status=dev.status)
+    return dict(records=rec, dt=dt, nt=nt, stats=mbs_scenario_stats(sc), counters=mbs_scenario_counters(sc),
+                device_status=dev.status)

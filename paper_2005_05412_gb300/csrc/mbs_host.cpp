@@ -1181,15 +1181,30 @@ static int prepare_solve(mbs_scenario_s *s, int prec, cudaStream_t st) {
 }
 
 // Tile depth when the caller leaves it to the library: the fastest measured
-// on GB300 (two levels: 24 steps, three levels: 32).
-static int default_tile_steps(int N) { return N == 2 ? 24 : 32; }
+// on GB300 (two levels: 24 steps, three levels: 32, tensor-core tiles: 8).
+static int default_tile_steps(int N) { return N == 2 ? 24 : N == 3 ? 32 : 8; }
+
+// Whether scenario s runs on the tensor-core tiles (N = 4..6 in FP32 with a
+// single medium and no per-cell operators).
+static bool uses_tc(const mbs_scenario_s *s, int prec) {
+  return s->N >= 4 && mbs::tiled_tc_supported(prec, s->N) && s->n_slot == 1 && !s->has_pcell;
+}
 
 static int default_algo(const mbs_scenario_s *s, int prec) {
+  if (uses_tc(s, prec)) return MBS_ALGO_TILED;
   return mbs::tiled_supported(prec, s->N) && (!s->has_pcell || s->N == 2) ? MBS_ALGO_TILED : MBS_ALGO_PLAIN;
 }
 
 // Whether the tiled kernels cover scenario s with tile depth T (sets the error).
 static int tiled_ok(const mbs_scenario_s *s, int prec, int T) {
+  if (s->N >= 4) {
+    if (!uses_tc(s, prec))
+      return fail(MBS_E_INVALID,
+                  "tiled kernels for N >= 4 need FP32, one medium and no per-cell factors; use the plain algorithm");
+    if (T < 1 || T > mbs::tiled_tc_max_steps())
+      return fail(MBS_E_INVALID, "tile_steps must be in [1, %d] for N >= 4", mbs::tiled_tc_max_steps());
+    return MBS_OK;
+  }
   if (!mbs::tiled_supported(prec, s->N) || (s->has_pcell && s->N != 2))
     return fail(MBS_E_INVALID, "tiled kernels cover N = 2 (also with per-cell factors) and N = 3");
   const int R = mbs::tile_lane_cells(s->N);
@@ -1240,6 +1255,7 @@ static int finish_solve(mbs_scenario_s *s, int prec, int cur) {
   } else {
     s->st_min = 0;
   }
+  if (flags[1]) return fail(MBS_E_TIMEOUT, "a bounded wait on the tensor cores gave up");
   if (flags[0]) return fail(MBS_E_NUMERIC, "non-finite density matrix");
   if (nchk && s->st_min < -1e-6) return fail(MBS_E_NUMERIC, "density matrix eigenvalue %.3g < -1e-6", s->st_min);
   return MBS_OK;
@@ -1259,7 +1275,7 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
     long long done = 0;
     while (done < s->nt) {
       const int ns = (int)std::min<long long>(T, s->nt - done);
-      int r = mbs::launch_tiled(a, done, ns, T, cur, st);
+      int r = s->N >= 4 ? mbs::launch_tiled_tc(a, done, ns, T, cur, st) : mbs::launch_tiled(a, done, ns, T, cur, st);
       ++s->launches;
       if (r) return cuda_fail((cudaError_t)r, "tiled launch");
       cur ^= 1;
@@ -1448,7 +1464,8 @@ int mbs_solve(mbs_scenario_t *batch, int n_scen, const mbs_opts *opts, void *cud
   // several scenarios on the tiled path advance together, unless asked not to
   bool batched = n_scen > 1 && !(o.flags & MBS_SOLVE_ONE_AT_A_TIME) && o.algo != MBS_ALGO_PLAIN &&
                  o.check_every == 0;
-  for (int i = 0; i < n_scen && batched; ++i) batched = default_algo(batch[i], o.precision) == MBS_ALGO_TILED;
+  for (int i = 0; i < n_scen && batched; ++i)
+    batched = batch[i]->N <= 3 && default_algo(batch[i], o.precision) == MBS_ALGO_TILED;
   if (batched) {
     std::vector<mbs_scenario_s *> ss(batch, batch + n_scen);
     return solve_batch(ss, o, st);

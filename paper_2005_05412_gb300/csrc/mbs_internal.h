@@ -119,4 +119,10 @@ int launch_tiled_batch(int prec, int N, int pm, const Args *args, const int2 *ta
 int launch_check(const Args &a, int cur, const int *cells, int n_cells, double *out_min_eig,
                  double *out_trace_dev, const void *zref_full, const void *V, void *stream);
 
+// Tensor-core tiled kernel for N = 4..6 (mbs_tc.cu): FP32 state, one medium
+// parameter slot, no per-cell operators, 1 <= T <= tiled_tc_max_steps().
+int tiled_tc_supported(int prec, int N);
+int tiled_tc_max_steps();
+int launch_tiled_tc(const Args &a, long long n0, int nsteps, int T, int cur, void *stream);
+
 }  // namespace mbs

@@ -1,0 +1,610 @@
+// mbs_tc.cu -- temporally tiled step for media with N >= 4 levels, the
+// constant propagator applied on the fifth-generation tensor cores.
+//
+// For N levels the Bloch deviation has K = N^2 - 1 components, and the
+// constant half of the Strang step (Sec. 2.2, exp(L0 dt) with H0 and the
+// Lindblad relaxation) is a dense K x K affine map -- 1,225 multiply-adds per
+// cell and step at N = 6, against ~150 for everything else a cell does.  This
+// kernel gives that contraction to tcgen05:
+//
+//   * a block of 128 threads owns one 128-cell tile (thread = cell = MMA row
+//     = TMEM lane) and advances it T steps per launch, with the same light-
+//     cone halo recompute, float-float fields and warp-edge exchange as the
+//     N = 2, 3 tiles (mbs_device.cuh);
+//   * per step each thread rotates its cell's coherences by the field angle
+//     (the exp(-i mu E dt) factor, exact in the mu eigenbasis) and writes the
+//     rotated deviation, augmented by a constant 1, to shared memory as two
+//     TF32 operands u = u_hi + u_lo (K-major, no swizzle);
+//   * one thread issues D = u_lo W_hi^T + u_hi W_lo^T + u_hi W_hi^T
+//     (3xTF32, FP32 accumulation in TMEM; M = 128 cells, N = outputs padded to
+//     16, K = inputs padded to 8).  W = [[A - I, c], [w, w0]] so that the MMA
+//     also forms the affine offset and the coupling w . u + w0 that drives E;
+//   * the threads read their row back (tcgen05.ld), add it to the deviation
+//     with Kahan compensation, and finish the field update.
+//
+// The tensor-core error is that of the 3xTF32 split (~2^-22 relative per
+// product), below the FP32 rounding of the state that the compensated sums
+// already absorb.  Every wait on the tensor core is bounded: on timeout the
+// block raises flags[1] (MBS_E_TIMEOUT on the host), frees its TMEM and
+// returns.
+#include "mbs_device.cuh"
+
+namespace mbs {
+namespace dev {
+
+template <int N>
+struct TcShape {
+  static constexpr int K = N * N - 1;                 // deviation components
+  static constexpr int P = N * (N - 1) / 2;           // coherence pairs
+  static constexpr int NP = N - 1;                    // population components
+  // TMEM column of deviation component i is i + SH: every coherence pair
+  // (NP + 2p, NP + 2p + 1) then starts on an even column and never straddles
+  // a 16-column chunk
+  static constexpr int SH = NP & 1;
+  static constexpr int KA = (K + 1 + 7) / 8 * 8;      // MMA K: [u, 1] padded to the TF32 K step (8)
+  static constexpr int NO = (K + SH + 1 + 15) / 16 * 16;   // MMA N: [0^SH, (A - I) u + c, w . u + w0], padded to 16
+  static constexpr int NCH = (K + SH + 15) / 16;      // 16-column chunks holding the K components
+  static constexpr int M = 128;                       // cells per tile = MMA M = threads per block
+  static constexpr int W = M / 32;                    // warps
+  // TMEM: accumulator columns [0, NO), Kahan compensation words [NO, 2 NO)
+  static constexpr int C_COL = NO;
+  static constexpr int TCOLS = 2 * NO <= 32 ? 32 : 2 * NO <= 64 ? 64 : 128;   // power of 2
+  static constexpr int CH = KA / 4;                   // 16-byte chunks per operand row
+  // canonical K-major layout without swizzle: 8-row x 16-byte core matrices,
+  // K-adjacent core matrices LBO bytes apart, row-adjacent ones SBO apart
+  static constexpr uint32_t LBO_A = M * 16, LBO_B = NO * 16, SBO = 128;
+  static constexpr uint32_t A_BYTES = M * KA * 4, B_BYTES = NO * KA * 4;
+  // dynamic shared memory: A_hi | A_lo | B_hi | B_lo | zr | edge slots | mbarrier, TMEM slot
+  static constexpr uint32_t OFF_ZR = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr uint32_t OFF_X = OFF_ZR + (2 * P + 3) / 4 * 16;
+  static constexpr uint32_t OFF_BAR = OFF_X + W * 16;
+  static constexpr uint32_t SMEM = OFF_BAR + 16;
+  static_assert(TCOLS >= 2 * NO, "accumulator and compensation words fit the TMEM allocation");
+  static_assert(NCH * 16 <= NO, "compensation chunks fit their columns");
+};
+
+// ------------------------------------------------------ tcgen05 primitives
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared-memory matrix descriptor (tcgen05): start address, leading- and
+// stride-dimension byte offsets (all >> 4), fixed version bits 46-48 = 0b001,
+// base offset 0, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+
+// instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
+// (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void bar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ bool bar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of the barrier, for at most ~1 s; false on timeout.
+__device__ __forceinline__ bool bar_wait_bounded(uint32_t bar, uint32_t parity) {
+  if (bar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!bar_try_wait(bar, parity))
+    if (global_ns() - t0 > 1000000000ull) return false;
+  return true;
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane; the wait takes the
+// registers as operands so that no use is scheduled before the data arrive
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15])::"memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// sin x and cos x - 1: Taylor polynomials for |x| <= 1/2 (as sincos_m1), the
+// library routine out of line otherwise, so that the many call sites of one
+// step stay small
+static __device__ __noinline__ void sincos_m1_far(float x, float &s, float &cm1) {
+  float c;
+  sincosf(x, &s, &c);
+  cm1 = c - 1.0f;
+}
+__device__ __forceinline__ void sincos_m1_tc(float x, float &s, float &cm1) {
+  const float t = x * x;
+  float ps = fmaf(t, 1.0f / 362880.0f, -1.0f / 5040.0f);
+  ps = fmaf(t, ps, 1.0f / 120.0f);
+  ps = fmaf(t, ps, -1.0f / 6.0f);
+  ps = fmaf(t, ps, 1.0f);
+  s = x * ps;
+  float pc = fmaf(t, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+  pc = fmaf(t, pc, -1.0f / 720.0f);
+  pc = fmaf(t, pc, 1.0f / 24.0f);
+  pc = fmaf(t, pc, -0.5f);
+  cm1 = t * pc;
+  if (fabsf(x) > 0.5f) sincos_m1_far(x, s, cm1);
+}
+
+// round to TF32 (10 explicit mantissa bits, nearest, ties away from zero)
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void sts128(uint32_t addr, float a, float b, float c, float d) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+// ---------------------------------------------------------------- kernel
+// Tile b owns cells [b*own, (b+1)*own), own = 128 - 2T; thread i holds cell
+// tb + i with tb = b*own - T (the tile holding the last cell may start 4 or 8
+// cells earlier, as in the N = 2, 3 tiles).  Requires one medium parameter
+// slot (slot 0) and no per-cell operators.  Reads buffers `cur`, writes the
+// owned cells of buffers cur ^ 1.
+//
+// Per thread the deviation lives in registers and its Kahan compensation in
+// the thread's TMEM lane (columns C_COL + i + SH), which keeps the block at
+// <= 128 registers per thread: four blocks (16 warps) per SM.
+template <int N>
+__global__ void __launch_bounds__(128, 4)
+    k_tiled_tc(const __grid_constant__ Args a, long long n0, int nsteps, int T, int cur) {
+  using S = TcShape<N>;
+  constexpr int K = S::K, P = S::P, NP = S::NP, SH = S::SH;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+  const int own = S::M - 2 * T;
+  const int c_own = blockIdx.x * own;
+  if (c_own >= a.nx) return;   // the whole block leaves together
+
+  const uint32_t sA_hi = smem_u32(smem), sA_lo = sA_hi + S::A_BYTES;
+  const uint32_t sB_hi = sA_lo + S::A_BYTES, sB_lo = sB_hi + S::B_BYTES;
+  float *s_zr = reinterpret_cast<float *>(smem + S::OFF_ZR);   // zr[2P]
+  float *s_x = reinterpret_cast<float *>(smem + S::OFF_X);     // [warp][E hi, E lo, H hi, H lo]
+  const uint32_t bar = smem_u32(smem + S::OFF_BAR);
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + S::OFF_BAR + 8);
+
+  // ---- weights W (rows = outputs): row i + SH = [(A - I)_i., c_i],
+  // row K + SH = [w, w0], other rows 0; as TF32 hi/lo
+  const float *mb = reinterpret_cast<const float *>(a.qpar);   // slot 0
+  const PrmBlock<float, N> q{mb};
+  for (int idx = tid; idx < S::NO * S::KA; idx += S::M) {
+    const int o = idx / S::KA, j = idx % S::KA, i = o - SH;
+    float v = 0.0f;
+    if (i >= 0 && i < K)
+      v = j < K ? q.am1(i, j) : (j == K ? q.c(i) : 0.0f);
+    else if (i == K)
+      v = j < K ? q.w(j) : (j == K ? q.w0() : 0.0f);
+    const float hi = to_tf32(v), lo = to_tf32(v - hi);
+    const uint32_t off = (uint32_t)(j >> 2) * S::LBO_B + (uint32_t)o * 16 + (uint32_t)(j & 3) * 4;
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(sB_hi + off), "f"(hi) : "memory");
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(sB_lo + off), "f"(lo) : "memory");
+  }
+  for (int i = tid; i < 2 * P; i += S::M) s_zr[i] = q.zr(i);
+  // field angles of the pairs (0, k), k = 1..N-1; every other pair's angle
+  // is a difference of two of them (theta_jk = theta_0k - theta_0j)
+  float kap0[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) kap0[k] = q.kap(k);
+  fence_async_smem();
+  if (tid == 0) bar_init(bar, 1);
+  if (wib == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                 "r"((uint32_t)S::TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+
+  // ---- tile geometry and this thread's cell
+  int tb = c_own - T;
+  if (a.nx - 1 < c_own + own) {
+    if (a.nx - 1 == c_own || (a.nx - 1 - tb) % 32 == 0) tb -= 4;
+    if ((a.nx - 1 - tb) % 32 == 0) tb -= 4;
+  }
+  const int lo = c_own - tb;      // tile position of the first owned cell
+  const int g0 = tb + tid;        // this thread's cell
+  const int base = a.off + g0;    // its array index (>= 0)
+
+  float E = reinterpret_cast<const float *>(a.E[cur])[base];
+  float El = reinterpret_cast<const float *>(a.El[cur])[base];
+  float H = reinterpret_cast<const float *>(a.H[cur])[base];
+  float Hl = reinterpret_cast<const float *>(a.Hl[cur])[base];
+  float d[K];
+  {
+    const float *Din = reinterpret_cast<const float *>(a.D[cur]);
+#pragma unroll
+    for (int i = 0; i < K; ++i) d[i] = Din[(size_t)i * a.ld + base];
+  }
+  const float *emc = reinterpret_cast<const float *>(a.emc);
+  const int mt = a.mat[base];
+  const float ca = emc[mt * 4 + 0], cb = emc[mt * 4 + 1];
+  const float ch = g0 == 0 ? 0.0f : emc[mt * 4 + 2];   // face 0 is a fixed boundary slot
+  const float mk = a.qslot[mt] >= 0 ? 1.0f : 0.0f;
+
+  const int t_lo = tb + wib * 32, t_hi = t_lo + 32;   // this warp's cells
+  bool any_src = false;
+  for (int s = 0; s < a.n_src; ++s)
+    any_src |= (a.src[s].cell >= t_lo && a.src[s].cell < t_hi) || (a.src[s].face >= t_lo && a.src[s].face < t_hi);
+  const bool any_bnd = (t_lo <= 0 && 0 < t_hi) || (t_lo <= a.nx - 1 && a.nx - 1 < t_hi);
+  const bool owned = tid >= lo && tid < lo + own && tid < S::M - T;
+  bool probe = false;
+  for (int p = 0; p < a.n_probe; ++p) probe |= owned && a.pr_cell[p] == g0;
+  float *rec = reinterpret_cast<float *>(a.rec);
+  const float *pcoef = reinterpret_cast<const float *>(a.pr_coef);
+
+  if (lane == 31) {
+    s_x[wib * 4 + 0] = E;
+    s_x[wib * 4 + 1] = El;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t t_row = tmem + ((uint32_t)(wib * 32) << 16);   // this warp's TMEM lanes
+  const uint32_t t_cmp = t_row + S::C_COL;                        // its compensation words
+  {
+    // compensation words of the cell into TMEM (column i + SH)
+    const float *Cin = reinterpret_cast<const float *>(a.C[cur]);
+#pragma unroll
+    for (int c16 = 0; c16 < S::NCH; ++c16) {
+      float v[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int i = 16 * c16 + e - SH;
+        v[e] = (i >= 0 && i < K) ? Cin[(size_t)i * a.ld + base] : 0.0f;
+      }
+      tmem_st16(t_cmp + 16 * c16, v);
+    }
+    tmem_wait_st();
+  }
+  constexpr uint32_t IDESC = idesc_tf32(S::M, S::NO);
+  const uint64_t dA_hi = umma_desc(sA_hi, S::LBO_A, S::SBO), dA_lo = umma_desc(sA_lo, S::LBO_A, S::SBO);
+  const uint64_t dB_hi = umma_desc(sB_hi, S::LBO_B, S::SBO), dB_lo = umma_desc(sB_lo, S::LBO_B, S::SBO);
+  uint32_t phase = 0;
+  bool timed_out = false;   // this thread's wait gave up
+  int stop = 0;             // some thread's wait gave up (block-uniform)
+
+  // A operand chunk c of this cell's row: [u, 1, 0...] elements 4c..4c+3 as TF32 hi and lo
+  auto put_a = [&](int c, const float (&u)[K]) {
+    float h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int j = 4 * c + e;
+      const float v = j < K ? u[j] : (j == K ? 1.0f : 0.0f);
+      h[e] = to_tf32(v);
+      l[e] = to_tf32(v - h[e]);
+    }
+    const uint32_t off = (uint32_t)c * S::LBO_A + (uint32_t)tid * 16;
+    sts128(sA_hi + off, h[0], h[1], h[2], h[3]);
+    sts128(sA_lo + off, l[0], l[1], l[2], l[3]);
+  };
+
+#pragma unroll 1
+  for (int t = 0; t < nsteps; ++t) {
+    const long long n = n0 + t;
+    // ---- H^{n+1/2} on the left face of the cell
+    {
+      float elh = __shfl_up_sync(FULL, E, 1), ell = __shfl_up_sync(FULL, El, 1);
+      if (lane == 0 && wib > 0) {
+        elh = s_x[(wib - 1) * 4 + 0];
+        ell = s_x[(wib - 1) * 4 + 1];
+      }
+      fld_axpy_diff<float, true>(H, Hl, ch, E, El, elh, ell, 0.0f);
+    }
+    if (any_src)
+      for (int s = 0; s < a.n_src; ++s)
+        if (a.src[s].face == g0) {
+          float vh, vl;
+          src_val<float>(a.src[s].sH, n, a.nt, vh, vl);
+          fld_add<float>(H, Hl, vh, vl);
+        }
+    if (lane == 0) {
+      s_x[wib * 4 + 2] = H;
+      s_x[wib * 4 + 3] = Hl;
+    }
+    // ---- field rotation, u = delta + (R - 1) x; the deviation takes the
+    // rotation now (compensated), the propagator's increment after the MMA
+    {
+      const float ej = fld_val<float>(E, El) * mk;
+      float sn[N], cm[N];   // sin, cos - 1 of theta_0k (k = 0: zero angle)
+      sn[0] = cm[0] = 0.0f;
+#pragma unroll
+      for (int k = 1; k < N; ++k) sincos_m1_tc(kap0[k - 1] * ej, sn[k], cm[k]);
+      float u[K];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) u[i] = d[i];
+      int a_done = 0;   // A chunks written so far
+#pragma unroll
+      for (int c16 = 0; c16 < S::NCH; ++c16) {
+        float cw[16];
+        tmem_ld16(t_cmp + 16 * c16, cw);
+#pragma unroll
+        for (int e = 0; e < 16; e += 2) {
+          const int i = 16 * c16 + e - SH;   // first component of a pair?
+          if (i < NP || i >= K) continue;
+          const int pr = (i - NP) / 2;
+          int j = 0, k = 0;                  // the pair's levels
+          for (int jj = 0, q2 = 0; jj < N; ++jj)
+            for (int kk = jj + 1; kk < N; ++kk, ++q2)
+              if (q2 == pr) { j = jj; k = kk; }
+          float s, m;
+          if (j == 0) {
+            s = sn[k];
+            m = cm[k];
+          } else {   // sin, cos - 1 of theta_0k - theta_0j
+            s = (sn[k] - sn[j]) + fmaf(sn[k], cm[j], -(cm[k] * sn[j]));
+            m = fmaf(cm[k], cm[j], fmaf(sn[k], sn[j], cm[k] + cm[j]));
+          }
+          const float2 z = reinterpret_cast<const float2 *>(s_zr)[pr];
+          const float xa = z.x + d[i], xb = z.y + d[i + 1];
+          const float ra = m * xa - s * xb;
+          const float rb = s * xa + m * xb;
+          u[i] = d[i] + ra;
+          u[i + 1] = d[i + 1] + rb;
+          kahan_add(d[i], cw[e], ra);
+          kahan_add(d[i + 1], cw[e + 1], rb);
+        }
+        tmem_st16(t_cmp + 16 * c16, cw);
+        const int ready = c16 == S::NCH - 1 ? S::CH : (16 * c16 + 16 - SH) / 4;   // chunks fully computed
+#pragma unroll
+        for (int c = 0; c < S::CH; ++c)
+          if (c >= a_done && c < ready) put_a(c, u);
+        a_done = ready;
+      }
+    }
+    tmem_wait_st();
+    fence_async_smem();
+    if (probe) {   // rho probes from the operand row (u = hi + lo to ~2^-22)
+      float u[K];
+#pragma unroll
+      for (int c = 0; c < S::CH; ++c) {
+        const float4 h = *reinterpret_cast<const float4 *>(smem + c * S::LBO_A + tid * 16);
+        const float4 l = *reinterpret_cast<const float4 *>(smem + S::A_BYTES + c * S::LBO_A + tid * 16);
+        const float hv[4] = {h.x, h.y, h.z, h.w}, lv[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (4 * c + e < K) u[4 * c + e] = hv[e] + lv[e];
+      }
+      for (int p = 0; p < a.n_probe; ++p)
+        if (a.pr_cell[p] == g0 && a.pr_q[p] >= 2)
+          rec[(size_t)p * a.nt + n] = probe_rho<float, N>(pcoef + (size_t)p * (K + 1), u);
+    }
+    tc_fence_before();
+    __syncthreads();   // operands written; H of the warp edges published
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int k = 0; k < S::KA / 8; ++k) {
+        const uint64_t oa = (uint64_t)((2 * k * S::LBO_A) >> 4), ob = (uint64_t)((2 * k * S::LBO_B) >> 4);
+        mma_tf32(tmem, dA_lo + oa, dB_hi + ob, IDESC, k > 0 ? 1u : 0u);
+        mma_tf32(tmem, dA_hi + oa, dB_lo + ob, IDESC, 1u);
+        mma_tf32(tmem, dA_hi + oa, dB_hi + ob, IDESC, 1u);
+      }
+      mma_commit(bar);
+    }
+    timed_out |= !bar_wait_bounded(bar, phase);
+    phase ^= 1u;
+    tc_fence_after();
+    // ---- delta += (A - I) u + c (compensated); coupling w . u + w0
+    float pw = 0.0f;
+#pragma unroll
+    for (int c16 = 0; c16 < S::NO / 16; ++c16) {
+      if (16 * c16 > K + SH) break;
+      float acc[16];
+      tmem_ld16(t_row + 16 * c16, acc);
+      if (c16 < S::NCH) {
+        float cw[16];
+        tmem_ld16(t_cmp + 16 * c16, cw);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int i = 16 * c16 + e - SH;
+          if (i >= 0 && i < K) kahan_add(d[i], cw[e], acc[e]);
+        }
+        tmem_st16(t_cmp + 16 * c16, cw);
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e)
+        if (16 * c16 + e - SH == K) pw = acc[e] * mk;
+    }
+    // ---- boundary cells: keep E^n of the boundary cell and its neighbour
+    float bo_h = 0.0f, bo_l = 0.0f, no_h = 0.0f, no_l = 0.0f;
+    if (any_bnd) {
+      const float r_oh = __shfl_down_sync(FULL, E, 1), r_ol = __shfl_down_sync(FULL, El, 1);
+      const float l_oh = __shfl_up_sync(FULL, E, 1), l_ol = __shfl_up_sync(FULL, El, 1);
+      if (g0 == 0) {
+        bo_h = E; bo_l = El; no_h = r_oh; no_l = r_ol;
+      }
+      if (g0 == a.nx - 1) {
+        bo_h = E; bo_l = El; no_h = l_oh; no_l = l_ol;
+      }
+    }
+    // ---- E^{n+1}
+    {
+      float hrh = __shfl_down_sync(FULL, H, 1), hrl = __shfl_down_sync(FULL, Hl, 1);
+      if (lane == 31 && wib < S::W - 1) {
+        hrh = s_x[(wib + 1) * 4 + 2];
+        hrl = s_x[(wib + 1) * 4 + 3];
+      }
+      fld_axpy_diff<float, true>(E, El, cb, hrh, hrl, H, Hl, ca * E - pw);
+    }
+    if (any_src)
+      for (int s = 0; s < a.n_src; ++s)
+        if (a.src[s].cell == g0) {
+          float vh, vl;
+          src_val<float>(a.src[s].sE, n, a.nt, vh, vl);
+          if (a.src[s].kind == 2) {
+            E = vh;
+            El = vl;
+          } else {
+            fld_add<float>(E, El, vh, vl);
+          }
+        }
+    if (any_bnd) {
+      // E_b^{n+1} = E_nb^n + k (E_nb^{n+1} - E_b^n), or 0 for a mirror
+      const float r_nh = __shfl_down_sync(FULL, E, 1), r_nl = __shfl_down_sync(FULL, El, 1);
+      const float l_nh = __shfl_up_sync(FULL, E, 1), l_nl = __shfl_up_sync(FULL, El, 1);
+      const bool lft = g0 == 0, rgt = g0 == a.nx - 1;
+      if (lft || rgt) {
+        const float nh = lft ? r_nh : l_nh, nl = lft ? r_nl : l_nl;
+        if ((lft ? a.bc_l : a.bc_r) == 1) {
+          E = El = 0.0f;
+        } else {
+          float bh = no_h, bl = no_l;
+          fld_axpy_diff<float>(bh, bl, float(lft ? a.kmur_l : a.kmur_r), nh, nl, bo_h, bo_l, 0.0f);
+          E = bh;
+          El = bl;
+        }
+      }
+    }
+    if (probe)
+      for (int p = 0; p < a.n_probe; ++p)
+        if (a.pr_cell[p] == g0 && a.pr_q[p] < 2)
+          rec[(size_t)p * a.nt + n] = a.pr_q[p] == 0 ? fld_val<float>(E, El) : fld_val<float>(H, Hl);
+    if (lane == 31) {
+      s_x[wib * 4 + 0] = E;
+      s_x[wib * 4 + 1] = El;
+    }
+    tmem_wait_st();
+    tc_fence_before();
+    stop = __syncthreads_or(timed_out);   // E of the warp edges published
+    if (stop) {
+      if (tid == 0) atomicOr(a.flags + 1, 1);
+      break;
+    }
+  }
+
+  // ---- compensation words back from TMEM, then release it (after a last
+  // bounded wait if a step gave up)
+  float cc[K];
+#pragma unroll
+  for (int c16 = 0; c16 < S::NCH; ++c16) {
+    float cw[16];
+    tmem_ld16(t_cmp + 16 * c16, cw);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int i = 16 * c16 + e - SH;
+      if (i >= 0 && i < K) cc[i] = cw[e];
+    }
+  }
+  if (stop && tid == 0) bar_wait_bounded(bar, phase ^ 1u);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (wib == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)S::TCOLS)
+                 : "memory");
+
+  // ---- write back the owned cells
+  if (!owned || g0 >= a.nx) return;
+  ff_renorm(E, El);
+  ff_renorm(H, Hl);
+  reinterpret_cast<float *>(a.E[cur ^ 1])[base] = E;
+  reinterpret_cast<float *>(a.El[cur ^ 1])[base] = El;
+  reinterpret_cast<float *>(a.H[cur ^ 1])[base] = H;
+  reinterpret_cast<float *>(a.Hl[cur ^ 1])[base] = Hl;
+  float *Do = reinterpret_cast<float *>(a.D[cur ^ 1]);
+  float *Co = reinterpret_cast<float *>(a.C[cur ^ 1]);
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    Do[(size_t)i * a.ld + base] = d[i];
+    Co[(size_t)i * a.ld + base] = cc[i];
+  }
+}
+
+template <int N>
+int tiled_tc_impl(const Args &a, long long n0, int nsteps, int T, int cur, cudaStream_t st) {
+  using S = TcShape<N>;
+  static_assert(S::M - 5 <= PAD, "a tile reaches past the pad cells");
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+  if (!attr_set[dev]) {
+    e = cudaFuncSetAttribute(k_tiled_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    if (e == cudaSuccess)   // all of the unified L1/shared storage as shared memory: 3 tiles per SM
+      e = cudaFuncSetAttribute(k_tiled_tc<N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return (int)e;
+    attr_set[dev] = true;
+  }
+  const int own = S::M - 2 * T;
+  const int gs = (a.nx + own - 1) / own;
+  k_tiled_tc<N><<<gs, S::M, S::SMEM, st>>>(a, n0, nsteps, T, cur);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace dev
+
+int tiled_tc_supported(int prec, int N) { return prec == 1 && N >= 4 && N <= 6; }
+
+int tiled_tc_max_steps() { return 20; }   // 32 - 12: room for the shift of the tile holding the last cell
+
+int launch_tiled_tc(const Args &a, long long n0, int nsteps, int T, int cur, void *stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (a.prec != 1 || a.n_slot != 1 || a.pcell || T < 1 || T > tiled_tc_max_steps())
+    return (int)cudaErrorInvalidValue;
+  switch (a.N) {
+    case 4: return dev::tiled_tc_impl<4>(a, n0, nsteps, T, cur, st);
+    case 5: return dev::tiled_tc_impl<5>(a, n0, nsteps, T, cur, st);
+    case 6: return dev::tiled_tc_impl<6>(a, n0, nsteps, T, cur, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace mbs
