@@ -390,6 +390,7 @@ struct Bundle {  // device buffers of one precision
   size_t rb = 8;
   void *E[2] = {}, *H[2] = {}, *El[2] = {}, *Hl[2] = {}, *D[2] = {}, *C[2] = {}, *pd = nullptr, *Dinit = nullptr;
   void *emc = nullptr, *qpar = nullptr, *pcell = nullptr, *pcell2 = nullptr, *pr_coef = nullptr, *rec = nullptr;
+  float *tcw = nullptr;
   std::vector<void *> src_tabs;
 };
 
@@ -402,6 +403,7 @@ struct mbs_scenario_s {
   int n_slot = 0, qstride = 0;
   // FP64 master copies
   std::vector<double> emc, qpar, pcell, pcell2, Dinit, pr_coef, zref;
+  std::vector<float> tcw;  // tensor-core tiles' constant table (N >= 4, one medium)
   bool has_b2 = false;   // structured two-level rows available (pcell2)
 
   std::vector<int> qslot, pr_cell, pr_q;
@@ -657,6 +659,7 @@ void free_bundle(Bundle &b) {
   cudaFree(b.pcell2);
   cudaFree(b.pr_coef);
   cudaFree(b.rec);
+  cudaFree(b.tcw);
   for (void *p : b.src_tabs) cudaFree(p);
   b = Bundle();
 }
@@ -687,6 +690,7 @@ int ensure_bundle(mbs_scenario_s *s, int prec) {
   if (s->has_pcell && (rc = upload(s->pcell, &b.pcell, prec))) return rc;
   if (s->has_b2 && (rc = upload(s->pcell2, &b.pcell2, prec))) return rc;
   if ((rc = upload(s->pr_coef, &b.pr_coef, prec))) return rc;
+  if (prec == 1 && !s->tcw.empty() && (rc = upload_raw(s->tcw, &b.tcw))) return rc;
   const size_t nrec = std::max<size_t>(1, s->pr_cell.size()) * (size_t)s->nt;
   if ((e = cudaMalloc(&b.rec, nrec * rb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc records");
   if ((e = cudaMemset(b.rec, 0, nrec * rb)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
@@ -747,6 +751,7 @@ mbs::Args make_args(mbs_scenario_s *s, int prec) {
   a.pr_cell = s->d_pr_cell;
   a.pr_q = s->d_pr_q;
   a.pr_coef = b.pr_coef;
+  a.tcw = b.tcw;
   a.rec = b.rec;
   a.flags = s->d_flags;
   return a;
@@ -955,6 +960,10 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
 
   for (double v : s->qpar)
     if (!std::isfinite(v)) return fail(MBS_E_NUMERIC, "non-finite step operator (check H0, mu, rates and dt)");
+  if (N >= 4 && s->n_slot == 1) {
+    s->tcw.resize(mbs::tc_weight_table(N, s->qpar.data(), nullptr));
+    mbs::tc_weight_table(N, s->qpar.data(), s->tcw.data());
+  }
 
   // per-cell state and (jittered media) per-cell step operators
   const int ld = s->ld, off = s->off;

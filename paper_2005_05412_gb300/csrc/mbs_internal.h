@@ -100,6 +100,7 @@ struct Args {
   const int *pr_cell;          // [n_probe]
   const int *pr_q;             // [n_probe] quantity
   const void *pr_coef;         // [n_probe][K+1]: rho probes h_K, h0
+  const float *tcw;            // tensor-core tiles: weight table (tc_weight_table) or null
   void *rec;                   // [n_probe][nt]
   int *flags;                  // [4] device status words
 };
@@ -124,5 +125,11 @@ int launch_check(const Args &a, int cur, const int *cells, int n_cells, double *
 int tiled_tc_supported(int prec, int N);
 int tiled_tc_max_steps();
 int launch_tiled_tc(const Args &a, long long n0, int nsteps, int T, int cur, void *stream);
+// Host: the tensor-core tiles' constant table for N levels from the FP64
+// parameter block of the medium (layout of q_stride): the TF32 hi/lo weight
+// operands in their shared-memory layout, the reference coherences and the
+// field angles of the pairs (0, k).  Returns the number of floats written
+// (out == nullptr: the number needed).
+int tc_weight_table(int N, const double *qblk, float *out);
 
 }  // namespace mbs

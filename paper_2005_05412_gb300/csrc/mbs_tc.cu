@@ -15,18 +15,21 @@
 //     (the exp(-i mu E dt) factor, exact in the mu eigenbasis) and writes the
 //     rotated deviation, augmented by a constant 1, to shared memory as two
 //     TF32 operands u = u_hi + u_lo (K-major, no swizzle);
-//   * one thread issues D = u_lo W_hi^T + u_hi W_lo^T + u_hi W_hi^T
+//   * one thread issues D += u_lo W_hi^T + u_hi W_lo^T + u_hi W_hi^T
 //     (3xTF32, FP32 accumulation in TMEM; M = 128 cells, N = outputs padded to
-//     16, K = inputs padded to 8).  W = [[A - I, c], [w, w0]] so that the MMA
-//     also forms the affine offset and the coupling w . u + w0 that drives E;
-//   * the threads read their row back (tcgen05.ld), add it to the deviation
-//     with Kahan compensation, and finish the field update.
+//     16, K = inputs padded to 8) onto D seeded by the threads with the
+//     rotation increments.  W = [[A - I, c], [w, w0]] so that the MMA also
+//     forms the affine offset and the coupling w . u + w0 that drives E;
+//   * the threads read their row back (tcgen05.ld), add the whole increment
+//     to the deviation with Kahan compensation, and finish the field update.
 //
 // The tensor-core error is that of the 3xTF32 split (~2^-22 relative per
 // product), below the FP32 rounding of the state that the compensated sums
 // already absorb.  Every wait on the tensor core is bounded: on timeout the
 // block raises flags[1] (MBS_E_TIMEOUT on the host), frees its TMEM and
 // returns.
+#include <cstring>
+
 #include "mbs_device.cuh"
 
 namespace mbs {
@@ -46,21 +49,44 @@ struct TcShape {
   static constexpr int NCH = (K + SH + 15) / 16;      // 16-column chunks holding the K components
   static constexpr int M = 128;                       // cells per tile = MMA M = threads per block
   static constexpr int W = M / 32;                    // warps
-  // TMEM: accumulator columns [0, NO), Kahan compensation words [NO, 2 NO)
+  // TMEM columns: accumulator [0, NO) (component i at column i + SH, the
+  // coupling at K + SH), Kahan compensation words [C_COL, C_COL + 16 NCH)
+  // in the same per-chunk positions.  Each step the threads seed the
+  // accumulator with the rotation increments (R - 1) x and the MMA adds the
+  // propagator's increment onto them.
   static constexpr int C_COL = NO;
-  static constexpr int TCOLS = 2 * NO <= 32 ? 32 : 2 * NO <= 64 ? 64 : 128;   // power of 2
+  static constexpr int TCOLS = C_COL + 16 * NCH <= 32 ? 32 : C_COL + 16 * NCH <= 64 ? 64 : 128;   // power of 2
+  static_assert(C_COL + 16 * NCH <= TCOLS, "TMEM columns");
   static constexpr int CH = KA / 4;                   // 16-byte chunks per operand row
   // canonical K-major layout without swizzle: 8-row x 16-byte core matrices,
   // K-adjacent core matrices LBO bytes apart, row-adjacent ones SBO apart
   static constexpr uint32_t LBO_A = M * 16, LBO_B = NO * 16, SBO = 128;
   static constexpr uint32_t A_BYTES = M * KA * 4, B_BYTES = NO * KA * 4;
-  // dynamic shared memory: A_hi | A_lo | B_hi | B_lo | zr | edge slots | mbarrier, TMEM slot
-  static constexpr uint32_t OFF_ZR = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr uint32_t OFF_X = OFF_ZR + (2 * P + 3) / 4 * 16;
-  static constexpr uint32_t OFF_BAR = OFF_X + W * 16;
+  // constant table (built on the host by tc_weight_table, copied verbatim):
+  // B_hi | B_lo in their shared-memory layout | zr[2P] | kap0[N-1], each
+  // part padded to whole 16-byte vectors
+  static constexpr int ZR4 = (2 * P + 3) / 4 * 4, KP4 = (NP + 3) / 4 * 4;
+  static constexpr int TAB = 2 * B_BYTES / 4 + ZR4 + KP4;   // floats
+  // dynamic shared memory: A_hi | A_lo | table | edge slots | probe cells,
+  // quantities | mbarrier, TMEM slot
+  static constexpr uint32_t OFF_TAB = 2 * A_BYTES;
+  static constexpr uint32_t OFF_ZR = OFF_TAB + 2 * B_BYTES;
+  static constexpr uint32_t OFF_KP = OFF_ZR + ZR4 * 4;
+  static constexpr uint32_t OFF_X = OFF_TAB + TAB * 4;
+  static constexpr uint32_t OFF_PR = OFF_X + W * 16;
+  static constexpr uint32_t OFF_BAR = OFF_PR + 2 * MAXPROBE * 4;
   static constexpr uint32_t SMEM = OFF_BAR + 16;
-  static_assert(TCOLS >= 2 * NO, "accumulator and compensation words fit the TMEM allocation");
   static_assert(NCH * 16 <= NO, "compensation chunks fit their columns");
+  // chunk of the seeded accumulator after which A chunk c (elements 4c..4c+3
+  // of [u, 1, 0...]) is known; -1: populations and constants only
+  __host__ __device__ static constexpr int a_step(int c) {
+    int st = -1;
+    for (int e = 0; e < 4; ++e) {
+      const int j = 4 * c + e;
+      if (j >= NP && j < K && (j + SH) / 16 > st) st = (j + SH) / 16;
+    }
+    return st;
+  }
 };
 
 // ------------------------------------------------------ tcgen05 primitives
@@ -102,13 +128,16 @@ __device__ __forceinline__ void bar_init(uint32_t bar, uint32_t count) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// One test of the barrier phase; a thread whose phase is not complete is
+// suspended (it issues nothing) until the phase completes or about 0.1 ms
+// pass, so that waiting warps leave the issue slots to the other blocks.
 __device__ __forceinline__ bool bar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(100000u)
       : "memory");
   return ok != 0;
 }
@@ -200,8 +229,8 @@ __device__ __forceinline__ void sts128(uint32_t addr, float a, float b, float c,
 // owned cells of buffers cur ^ 1.
 //
 // Per thread the deviation lives in registers and its Kahan compensation in
-// the thread's TMEM lane (columns C_COL + i + SH), which keeps the block at
-// <= 128 registers per thread: four blocks (16 warps) per SM.
+// the thread's TMEM lane, which keeps the block at <= 128 registers per
+// thread: four blocks (16 warps) per SM.
 template <int N>
 __global__ void __launch_bounds__(128, 4)
     k_tiled_tc(const __grid_constant__ Args a, long long n0, int nsteps, int T, int cur) {
@@ -215,33 +244,29 @@ __global__ void __launch_bounds__(128, 4)
 
   const uint32_t sA_hi = smem_u32(smem), sA_lo = sA_hi + S::A_BYTES;
   const uint32_t sB_hi = sA_lo + S::A_BYTES, sB_lo = sB_hi + S::B_BYTES;
-  float *s_zr = reinterpret_cast<float *>(smem + S::OFF_ZR);   // zr[2P]
+  const float *s_zr = reinterpret_cast<const float *>(smem + S::OFF_ZR);   // zr[2P]
+  const int *s_pc = reinterpret_cast<const int *>(smem + S::OFF_PR);         // probe cells | quantities
   float *s_x = reinterpret_cast<float *>(smem + S::OFF_X);     // [warp][E hi, E lo, H hi, H lo]
   const uint32_t bar = smem_u32(smem + S::OFF_BAR);
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + S::OFF_BAR + 8);
 
-  // ---- weights W (rows = outputs): row i + SH = [(A - I)_i., c_i],
-  // row K + SH = [w, w0], other rows 0; as TF32 hi/lo
-  const float *mb = reinterpret_cast<const float *>(a.qpar);   // slot 0
-  const PrmBlock<float, N> q{mb};
-  for (int idx = tid; idx < S::NO * S::KA; idx += S::M) {
-    const int o = idx / S::KA, j = idx % S::KA, i = o - SH;
-    float v = 0.0f;
-    if (i >= 0 && i < K)
-      v = j < K ? q.am1(i, j) : (j == K ? q.c(i) : 0.0f);
-    else if (i == K)
-      v = j < K ? q.w(j) : (j == K ? q.w0() : 0.0f);
-    const float hi = to_tf32(v), lo = to_tf32(v - hi);
-    const uint32_t off = (uint32_t)(j >> 2) * S::LBO_B + (uint32_t)o * 16 + (uint32_t)(j & 3) * 4;
-    asm volatile("st.shared.f32 [%0], %1;" ::"r"(sB_hi + off), "f"(hi) : "memory");
-    asm volatile("st.shared.f32 [%0], %1;" ::"r"(sB_lo + off), "f"(lo) : "memory");
-  }
-  for (int i = tid; i < 2 * P; i += S::M) s_zr[i] = q.zr(i);
-  // field angles of the pairs (0, k), k = 1..N-1; every other pair's angle
-  // is a difference of two of them (theta_jk = theta_0k - theta_0j)
-  float kap0[NP];
+  // ---- constant table: weights W (rows = outputs; row i + SH =
+  // [(A - I)_i., c_i], row K + SH = [w, w0], other rows 0) as TF32 hi/lo,
+  // reference coherences, field angles of the pairs (0, k); probe tables
+  {
+    const float4 *src = reinterpret_cast<const float4 *>(a.tcw);
+    float4 *dst = reinterpret_cast<float4 *>(smem + S::OFF_TAB);
 #pragma unroll
-  for (int k = 0; k < NP; ++k) kap0[k] = q.kap(k);
+    for (int r = 0; r < (S::TAB / 4 + S::M - 1) / S::M; ++r) {
+      const int i = tid + r * S::M;
+      if (i < S::TAB / 4) dst[i] = src[i];
+    }
+    int *pw_ = reinterpret_cast<int *>(smem + S::OFF_PR);
+    if (tid < a.n_probe) {
+      pw_[tid] = a.pr_cell[tid];
+      pw_[MAXPROBE + tid] = a.pr_q[tid];
+    }
+  }
   fence_async_smem();
   if (tid == 0) bar_init(bar, 1);
   if (wib == 0) {
@@ -283,8 +308,6 @@ __global__ void __launch_bounds__(128, 4)
     any_src |= (a.src[s].cell >= t_lo && a.src[s].cell < t_hi) || (a.src[s].face >= t_lo && a.src[s].face < t_hi);
   const bool any_bnd = (t_lo <= 0 && 0 < t_hi) || (t_lo <= a.nx - 1 && a.nx - 1 < t_hi);
   const bool owned = tid >= lo && tid < lo + own && tid < S::M - T;
-  bool probe = false;
-  for (int p = 0; p < a.n_probe; ++p) probe |= owned && a.pr_cell[p] == g0;
   float *rec = reinterpret_cast<float *>(a.rec);
   const float *pcoef = reinterpret_cast<const float *>(a.pr_coef);
 
@@ -296,6 +319,13 @@ __global__ void __launch_bounds__(128, 4)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
+  bool probe = false;
+  for (int p = 0; p < a.n_probe; ++p) probe |= owned && s_pc[p] == g0;
+  // field angles of the pairs (0, k), k = 1..N-1; every other pair's angle
+  // is a difference of two of them (theta_jk = theta_0k - theta_0j)
+  float kap0[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) kap0[k] = reinterpret_cast<const float *>(smem + S::OFF_KP)[k];
   const uint32_t t_row = tmem + ((uint32_t)(wib * 32) << 16);   // this warp's TMEM lanes
   const uint32_t t_cmp = t_row + S::C_COL;                        // its compensation words
   {
@@ -358,8 +388,8 @@ __global__ void __launch_bounds__(128, 4)
       s_x[wib * 4 + 2] = H;
       s_x[wib * 4 + 3] = Hl;
     }
-    // ---- field rotation, u = delta + (R - 1) x; the deviation takes the
-    // rotation now (compensated), the propagator's increment after the MMA
+    // ---- field rotation, u = delta + (R - 1) x; the increments (R - 1) x
+    // seed the accumulator, the MMA adds (A - I) u + c to them
     {
       const float ej = fld_val<float>(E, El) * mk;
       float sn[N], cm[N];   // sin, cos - 1 of theta_0k (k = 0: zero angle)
@@ -369,11 +399,14 @@ __global__ void __launch_bounds__(128, 4)
       float u[K];
 #pragma unroll
       for (int i = 0; i < NP; ++i) u[i] = d[i];
-      int a_done = 0;   // A chunks written so far
 #pragma unroll
-      for (int c16 = 0; c16 < S::NCH; ++c16) {
-        float cw[16];
-        tmem_ld16(t_cmp + 16 * c16, cw);
+      for (int c = 0; c < S::CH; ++c)
+        if (S::a_step(c) < 0) put_a(c, u);
+#pragma unroll
+      for (int c16 = 0; c16 < S::NO / 16; ++c16) {
+        float seed[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) seed[e] = 0.0f;
 #pragma unroll
         for (int e = 0; e < 16; e += 2) {
           const int i = 16 * c16 + e - SH;   // first component of a pair?
@@ -383,29 +416,27 @@ __global__ void __launch_bounds__(128, 4)
           for (int jj = 0, q2 = 0; jj < N; ++jj)
             for (int kk = jj + 1; kk < N; ++kk, ++q2)
               if (q2 == pr) { j = jj; k = kk; }
-          float s, m;
+          float sv, mv;
           if (j == 0) {
-            s = sn[k];
-            m = cm[k];
+            sv = sn[k];
+            mv = cm[k];
           } else {   // sin, cos - 1 of theta_0k - theta_0j
-            s = (sn[k] - sn[j]) + fmaf(sn[k], cm[j], -(cm[k] * sn[j]));
-            m = fmaf(cm[k], cm[j], fmaf(sn[k], sn[j], cm[k] + cm[j]));
+            sv = (sn[k] - sn[j]) + fmaf(sn[k], cm[j], -(cm[k] * sn[j]));
+            mv = fmaf(cm[k], cm[j], fmaf(sn[k], sn[j], cm[k] + cm[j]));
           }
           const float2 z = reinterpret_cast<const float2 *>(s_zr)[pr];
           const float xa = z.x + d[i], xb = z.y + d[i + 1];
-          const float ra = m * xa - s * xb;
-          const float rb = s * xa + m * xb;
+          const float ra = mv * xa - sv * xb;
+          const float rb = sv * xa + mv * xb;
           u[i] = d[i] + ra;
           u[i + 1] = d[i + 1] + rb;
-          kahan_add(d[i], cw[e], ra);
-          kahan_add(d[i + 1], cw[e + 1], rb);
+          seed[e] = ra;
+          seed[e + 1] = rb;
         }
-        tmem_st16(t_cmp + 16 * c16, cw);
-        const int ready = c16 == S::NCH - 1 ? S::CH : (16 * c16 + 16 - SH) / 4;   // chunks fully computed
+        tmem_st16(t_row + 16 * c16, seed);
 #pragma unroll
         for (int c = 0; c < S::CH; ++c)
-          if (c >= a_done && c < ready) put_a(c, u);
-        a_done = ready;
+          if (S::a_step(c) == c16) put_a(c, u);
       }
     }
     tmem_wait_st();
@@ -422,7 +453,7 @@ __global__ void __launch_bounds__(128, 4)
           if (4 * c + e < K) u[4 * c + e] = hv[e] + lv[e];
       }
       for (int p = 0; p < a.n_probe; ++p)
-        if (a.pr_cell[p] == g0 && a.pr_q[p] >= 2)
+        if (s_pc[p] == g0 && s_pc[MAXPROBE + p] >= 2)
           rec[(size_t)p * a.nt + n] = probe_rho<float, N>(pcoef + (size_t)p * (K + 1), u);
     }
     tc_fence_before();
@@ -432,7 +463,7 @@ __global__ void __launch_bounds__(128, 4)
 #pragma unroll
       for (int k = 0; k < S::KA / 8; ++k) {
         const uint64_t oa = (uint64_t)((2 * k * S::LBO_A) >> 4), ob = (uint64_t)((2 * k * S::LBO_B) >> 4);
-        mma_tf32(tmem, dA_lo + oa, dB_hi + ob, IDESC, k > 0 ? 1u : 0u);
+        mma_tf32(tmem, dA_lo + oa, dB_hi + ob, IDESC, 1u);
         mma_tf32(tmem, dA_hi + oa, dB_lo + ob, IDESC, 1u);
         mma_tf32(tmem, dA_hi + oa, dB_hi + ob, IDESC, 1u);
       }
@@ -441,7 +472,7 @@ __global__ void __launch_bounds__(128, 4)
     timed_out |= !bar_wait_bounded(bar, phase);
     phase ^= 1u;
     tc_fence_after();
-    // ---- delta += (A - I) u + c (compensated); coupling w . u + w0
+    // ---- delta += (R - 1) x + (A - I) u + c (compensated); coupling w . u + w0
     float pw = 0.0f;
 #pragma unroll
     for (int c16 = 0; c16 < S::NO / 16; ++c16) {
@@ -514,8 +545,8 @@ __global__ void __launch_bounds__(128, 4)
     }
     if (probe)
       for (int p = 0; p < a.n_probe; ++p)
-        if (a.pr_cell[p] == g0 && a.pr_q[p] < 2)
-          rec[(size_t)p * a.nt + n] = a.pr_q[p] == 0 ? fld_val<float>(E, El) : fld_val<float>(H, Hl);
+        if (s_pc[p] == g0 && s_pc[MAXPROBE + p] < 2)
+          rec[(size_t)p * a.nt + n] = s_pc[MAXPROBE + p] == 0 ? fld_val<float>(E, El) : fld_val<float>(H, Hl);
     if (lane == 31) {
       s_x[wib * 4 + 0] = E;
       s_x[wib * 4 + 1] = El;
@@ -591,13 +622,62 @@ int tiled_tc_impl(const Args &a, long long n0, int nsteps, int T, int cur, cudaS
 
 }  // namespace dev
 
+namespace {
+// round to TF32: nearest, ties away from zero (10 explicit mantissa bits)
+float tf32_host(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  b = (b + 0x1000u) & 0xFFFFE000u;
+  float y;
+  std::memcpy(&y, &b, 4);
+  return y;
+}
+
+template <int N>
+int tc_table_impl(const double *qb, float *out) {
+  using S = dev::TcShape<N>;
+  if (!out) return S::TAB;
+  constexpr int K = S::K, P = S::P;
+  for (int i = 0; i < S::TAB; ++i) out[i] = 0.0f;
+  float *bh = out, *bl = out + S::B_BYTES / 4;
+  auto at = [&](int i, int j) { return qb[i * K + j]; };   // (A - I) row-major
+  for (int o = 0; o < S::NO; ++o)
+    for (int j = 0; j < S::KA; ++j) {
+      const int i = o - S::SH;
+      double v = 0.0;
+      if (i >= 0 && i < K)
+        v = j < K ? at(i, j) : (j == K ? qb[K * K + i] : 0.0);
+      else if (i == K)
+        v = j < K ? qb[K * K + K + j] : (j == K ? qb[K * K + 2 * K] : 0.0);
+      const float hi = tf32_host((float)v);
+      const float lo = tf32_host((float)(v - (double)hi));
+      const int idx = ((j >> 2) * (int)S::LBO_B + o * 16 + (j & 3) * 4) / 4;
+      bh[idx] = hi;
+      bl[idx] = lo;
+    }
+  float *zr = out + 2 * S::B_BYTES / 4, *kp = zr + S::ZR4;
+  for (int i = 0; i < 2 * P; ++i) zr[i] = (float)qb[K * K + 2 * K + 1 + P + i];
+  for (int k = 0; k < S::NP; ++k) kp[k] = (float)qb[K * K + 2 * K + 1 + k];
+  return S::TAB;
+}
+}  // namespace
+
+int tc_weight_table(int N, const double *qblk, float *out) {
+  switch (N) {
+    case 4: return tc_table_impl<4>(qblk, out);
+    case 5: return tc_table_impl<5>(qblk, out);
+    case 6: return tc_table_impl<6>(qblk, out);
+  }
+  return 0;
+}
+
 int tiled_tc_supported(int prec, int N) { return prec == 1 && N >= 4 && N <= 6; }
 
 int tiled_tc_max_steps() { return 20; }   // 32 - 12: room for the shift of the tile holding the last cell
 
 int launch_tiled_tc(const Args &a, long long n0, int nsteps, int T, int cur, void *stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (a.prec != 1 || a.n_slot != 1 || a.pcell || T < 1 || T > tiled_tc_max_steps())
+  if (a.prec != 1 || a.n_slot != 1 || a.pcell || !a.tcw || a.n_probe > MAXPROBE || T < 1 || T > tiled_tc_max_steps())
     return (int)cudaErrorInvalidValue;
   switch (a.N) {
     case 4: return dev::tiled_tc_impl<4>(a, n0, nsteps, T, cur, st);
