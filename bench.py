@@ -194,21 +194,24 @@ def run_ours(args, rank, world, local):
     hbm = pk.get("hbm_gbs")
     # roofline of the dominant kernel (the tiled step): algorithmic bytes per
     # cell-step = (2 + K) state values read + written, plus the 2 read-only
-    # per-cell parameters of the jittered medium
-    K = 3
+    # per-cell parameters of a jittered medium
+    n_lv = p.qms[0].n_levels
+    K = n_lv * n_lv - 1
+    jit = p.jitter is not None
     rb = 4 if args.precision == "fp32" else 8
-    alg_bytes = (2 * (2 + K) + 2) * rb
+    alg_bytes = (2 * (2 + K) + (2 if jit else 0)) * rb
     tiled_launches = math.ceil(p.n_steps / T)
     per_launch_s = t_local / args.steps / max(1, launches)
     units_per_launch = p.n_cells * T
     achieved = alg_bytes * units_per_launch / per_launch_s / 1e9
-    prof = load_profile(args)
+    prof = load_profile(f"{args.workload}_{args.precision}_T{args.tile}")
     traffic = prof.get("dram_bytes") if prof else None
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm or HBM_FALLBACK, "unit": "GB/s",
             "frac": round(achieved / (hbm or HBM_FALLBACK), 4), "traffic": traffic,
             "peak_source": "measured" if hbm else "fallback",
             "binding": "instruction issue (temporal tiles keep the state on chip; see issue)",
-            "kernel": f"k_tiled<{args.precision},N=2,percell> T={T}",
+            "kernel": (f"k_tiled_tc<{n_lv}> (tcgen05 3xTF32)" if n_lv >= 4 else
+                       f"k_tiled<{args.precision},N={n_lv}{',percell' if jit else ''}>") + f" T={T}",
             "alg_bytes_per_cell_step": alg_bytes, "launch_ms": round(per_launch_s * 1e3, 5),
             "launches_per_solve": launches, "tiled_launches_per_solve": tiled_launches}
     clocks = clk.summary()
@@ -224,13 +227,16 @@ def run_ours(args, rank, world, local):
            "warmup": args.warmup, "ms_per_step": round(t_max * 1e3 / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
            "data": "synthetic (seeded)",
-           "config": {"workload": f"{p.name}: {p.n_cells} cells x {p.n_steps} steps, N=2, per-cell jitter",
+           "config": {"workload": f"{p.name}: {p.n_cells} cells x {p.n_steps} steps, N={n_lv}"
+                                  + (", per-cell jitter" if jit else ""),
                       "precision": args.precision, "algo": "tiled", "tile_steps": T,
                       "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)"},
            "roofline": roof, "clocks": clocks, "gpu_launches": launches * args.steps,
            "wall_s": round(wall, 3)}
     if rank == 0 and not args.quick:
         out["fp64_plain"] = fp64_plain(p, mbs, stream, torch)
+        out["six_level"] = level_leg(mbs, stream, torch, "ladder_6lvl", 10, pk, clocks)
+        out["three_level"] = level_leg(mbs, stream, torch, "lambda_3lvl", 0, pk, clocks)
         if not args.no_batch:
             out["batch"] = batch_leg(mbs, stream, torch, args.precision)
         out["e2e"] = e2e(p, mbs, args, torch, stream)
@@ -240,6 +246,78 @@ def run_ours(args, rank, world, local):
                                    "kind": "oracle", "sample": cb["sample"]}
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+# bytes of algorithmic state per cell-step (2 + K values read and written)
+def state_bytes(n_levels, rb=4):
+    return 2 * (2 + n_levels * n_levels - 1) * rb
+
+
+def level_leg(mbs, stream, torch, name, T, pk, clocks, reps=2, fp64_steps=1000):
+    """One whole simulation of the multi-level workloads at full size (the
+    six-level ladder, 131,072 cells x 50,000 steps, on the tensor-core tiles;
+    the three-level Lambda medium, 262,144 cells x 100,000 steps), FP32, with
+    the FP32 and FP64 plain paths timed on their first steps."""
+    p = W.WORKLOADS[name]()
+    n = p.qms[0].n_levels
+    K = n * n - 1
+    dev = mbs.device_from_problem(p)
+    sc = mbs.scenario_from_problem(dev, p)
+
+    def timed(scn, prec, algo, tile):
+        mbs.mbs_solve([scn], prec, algo, tile_steps=tile, stream=stream.cuda_stream)   # warm-up
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mbs.mbs_solve([scn], prec, algo, tile_steps=tile, stream=stream.cuda_stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3
+            best = t if best is None else min(best, t)
+        return best
+
+    t = timed(sc, "fp32", "tiled", T)
+    launches = mbs.mbs_scenario_counters(sc)["kernel_launches"]
+    Teff = T if T else (24 if n == 2 else 32)
+    value = p.n_cells * p.n_steps / t / 1e9
+    hbm = pk.get("hbm_gbs") or HBM_FALLBACK
+    per_launch = t / max(1, launches)
+    out = {"value": round(value, 3), "unit": METRIC,
+           "workload": f"{p.name}: {p.n_cells} cells x {p.n_steps} steps, N={n}", "precision": "fp32",
+           "tile_steps": Teff}
+    hb = {"bound": "hbm", "achieved": round(state_bytes(n) * value, 1), "peak": hbm, "unit": "GB/s",
+          "frac": round(state_bytes(n) * value / hbm, 4), "alg_bytes_per_cell_step": state_bytes(n),
+          "peak_source": "measured" if pk.get("hbm_gbs") else "fallback", "launch_ms": round(per_launch * 1e3, 5)}
+    prof = load_profile(f"{name}_fp32_T{Teff}")
+    hb["traffic"] = prof.get("dram_bytes") if prof else None
+    out["roofline"] = hb
+    if n >= 4:
+        # the propagator apply on the tensor cores: 2 K^2 useful flops per
+        # cell-step; the 3xTF32 MMAs execute 3 x 2 x NO x KA per computed cell
+        sh = (n - 1) & 1
+        ka = (K + 1 + 7) // 8 * 8
+        no = (K + sh + 1 + 15) // 16 * 16
+        own = 128 - 2 * Teff
+        bf16 = pk.get("bf16_tflops")
+        tf32 = bf16 * 1.1 / 2.25 if bf16 else 1900.0 * 1.1 / 2.25
+        exec_tf = 3 * 2 * no * ka * value * 1e9 * 128 / own / 1e12
+        out["tensor"] = {"bound": "tensor", "achieved": round(exec_tf, 1), "peak": round(tf32, 1),
+                         "unit": "TFLOP/s", "frac": round(exec_tf / tf32, 4),
+                         "useful_tflops": round(2 * K * K * value * 1e9 / 1e12, 2),
+                         "peak_source": ("measured bf16 x nominal tf32/bf16 (1.1/2.25)" if bf16
+                                         else "fallback bf16 x nominal tf32/bf16"),
+                         "kernel": f"k_tiled_tc<{n}> (tcgen05 kind::tf32, 3xTF32, M=128 N={no} K={ka})"}
+    q = p.replace(n_steps=fp64_steps)
+    dq = mbs.device_from_problem(q)
+    sq = mbs.scenario_from_problem(dq, q)
+    for prec in ("fp32", "fp64"):
+        tq = timed(sq, prec, "plain", 0)
+        out[f"{prec}_plain"] = round(q.n_cells * q.n_steps / tq / 1e9, 3)
+    out["plain_sample"] = f"first {fp64_steps} steps"
+    out["speedup_vs_fp64_plain"] = round(value / out["fp64_plain"], 1)
+    return out
 
 
 def batch_leg(mbs, stream, torch, precision, T=0):
@@ -314,21 +392,22 @@ def e2e(p, mbs, args, torch, stream, reps=2):
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "seconds_per_step": round(t, 3)}
 
 
-def load_profile(args):
-    """ncu figures per launch of the dominant kernel (DRAM bytes, warp
-    instructions) from the committed summary profiles/traffic.json, or None
-    when the kernel source changed after the capture (the file records a hash
-    of the source it measured) or no capture exists for this tile depth."""
+def load_profile(key):
+    """ncu figures per launch of a kernel (DRAM bytes, warp instructions)
+    from the committed summary profiles/traffic.json, or None when no
+    capture exists for `key` or its kernel sources changed after the capture
+    (each entry records a hash of the sources it measured)."""
     import hashlib
     f = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(f))
+        e = d[key]
         h = hashlib.sha256()
-        for name in d["sources"]:
+        for name in e["sources"]:
             h.update(open(os.path.join(ROOT, name), "rb").read())
-        if h.hexdigest()[:16] != d["kernel_source_sha256_16"]:
+        if h.hexdigest()[:16] != e["kernel_source_sha256_16"]:
             return None
-        return d.get(f"{args.precision}_T{args.tile}")
+        return e
     except Exception:
         return None
 
@@ -351,7 +430,8 @@ def run_reference(args, rank, world):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs * 1e3 / args.steps, 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded)",
-           "config": {"workload": f"{p.name}: {p.n_cells} cells x {p.n_steps} steps, N=2, per-cell jitter",
+           "config": {"workload": f"{p.name}: {p.n_cells} cells x {p.n_steps} steps, N={n_lv}"
+                                  + (", per-cell jitter" if jit else ""),
                       "precision": "fp64", "algo": "oracle (CPU, OpenMP over cells)"},
            "cpu_baseline": {"value": round(value, 5), "unit": METRIC, "cores": vals[0]["cores"], "kind": "oracle",
                             "sample": vals[0]["sample"]},
