@@ -292,6 +292,12 @@ def level_leg(mbs, stream, torch, name, T, pk, clocks, reps=2, fp64_steps=1000):
           "peak_source": "measured" if pk.get("hbm_gbs") else "fallback", "launch_ms": round(per_launch * 1e3, 5)}
     prof = load_profile(f"{name}_fp32_T{Teff}")
     hb["traffic"] = prof.get("dram_bytes") if prof else None
+    if prof and prof.get("warp_inst") and clocks.get("sm_mhz"):
+        ach = prof["warp_inst"] / per_launch / 1e9
+        pk_i = 4 * 152 * clocks["sm_mhz"] / 1e3
+        hb["issue"] = {"achieved": round(ach, 1), "peak": round(pk_i, 1), "unit": "Gwarp-inst/s",
+                       "frac": round(ach / pk_i, 4), "warp_inst_per_launch": prof["warp_inst"],
+                       "source": "ncu smsp__inst_executed.sum of the same kernel and tile depth"}
     out["roofline"] = hb
     if n >= 4:
         # the propagator apply on the tensor cores: 2 K^2 useful flops per

@@ -323,9 +323,7 @@ __global__ void __launch_bounds__(128, 4)
   for (int p = 0; p < a.n_probe; ++p) probe |= owned && s_pc[p] == g0;
   // field angles of the pairs (0, k), k = 1..N-1; every other pair's angle
   // is a difference of two of them (theta_jk = theta_0k - theta_0j)
-  float kap0[NP];
-#pragma unroll
-  for (int k = 0; k < NP; ++k) kap0[k] = reinterpret_cast<const float *>(smem + S::OFF_KP)[k];
+  const float *kap0 = reinterpret_cast<const float *>(smem + S::OFF_KP);
   const uint32_t t_row = tmem + ((uint32_t)(wib * 32) << 16);   // this warp's TMEM lanes
   const uint32_t t_cmp = t_row + S::C_COL;                        // its compensation words
   {
@@ -344,8 +342,6 @@ __global__ void __launch_bounds__(128, 4)
     tmem_wait_st();
   }
   constexpr uint32_t IDESC = idesc_tf32(S::M, S::NO);
-  const uint64_t dA_hi = umma_desc(sA_hi, S::LBO_A, S::SBO), dA_lo = umma_desc(sA_lo, S::LBO_A, S::SBO);
-  const uint64_t dB_hi = umma_desc(sB_hi, S::LBO_B, S::SBO), dB_lo = umma_desc(sB_lo, S::LBO_B, S::SBO);
   uint32_t phase = 0;
   bool timed_out = false;   // this thread's wait gave up
   int stop = 0;             // some thread's wait gave up (block-uniform)
@@ -460,6 +456,8 @@ __global__ void __launch_bounds__(128, 4)
     __syncthreads();   // operands written; H of the warp edges published
     if (tid == 0) {
       tc_fence_after();
+      const uint64_t dA_hi = umma_desc(sA_hi, S::LBO_A, S::SBO), dA_lo = umma_desc(sA_lo, S::LBO_A, S::SBO);
+      const uint64_t dB_hi = umma_desc(sB_hi, S::LBO_B, S::SBO), dB_lo = umma_desc(sB_lo, S::LBO_B, S::SBO);
 #pragma unroll
       for (int k = 0; k < S::KA / 8; ++k) {
         const uint64_t oa = (uint64_t)((2 * k * S::LBO_A) >> 4), ob = (uint64_t)((2 * k * S::LBO_B) >> 4);
