@@ -113,6 +113,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- ranks
+def max_over_ranks(t_local, world, device):
+    """The slowest rank's time (an all-reduce MAX over the process group)."""
+    if world == 1:
+        return t_local
+    import torch
+    t = torch.tensor([t_local], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(cell_steps, steps, world, t_max):
+    """Whole-job throughput [Gcell-steps/s]: every rank solves its own replica
+    of the workload `steps` times; all ranks' cell-steps over the slowest
+    rank's time."""
+    return cell_steps * steps * world / t_max / 1e9
+
+
 # ---------------------------------------------------------------- CPU oracle
 def cpu_sample(p, cells, steps):
     """A slab of the workload for timing the oracle: `cells` consecutive
@@ -181,15 +199,10 @@ def run_ours(args, rank, world, local):
         torch.distributed.barrier()
     dev_ms = sum(a.elapsed_time(b) for a, b in ev)
     t_local = dev_ms / 1e3
-    if world > 1:
-        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
+    t_max = max_over_ranks(t_local, world, "cuda")
     ctr = mbs.mbs_scenario_counters(sc)
     launches = ctr["kernel_launches"]
-    value = cell_steps * args.steps * world / t_max / 1e9
+    value = job_value(cell_steps, args.steps, world, t_max)
     pk = peaks()
     hbm = pk.get("hbm_gbs")
     # roofline of the dominant kernel (the tiled step): algorithmic bytes per
@@ -235,10 +248,10 @@ def run_ours(args, rank, world, local):
            "wall_s": round(wall, 3)}
     if rank == 0 and not args.quick:
         out["fp64_plain"] = fp64_plain(p, mbs, stream, torch)
-        out["six_level"] = level_leg(mbs, stream, torch, "ladder_6lvl", 10, pk, clocks)
+        out["six_level"] = level_leg(mbs, stream, torch, "ladder_6lvl", 0, pk, clocks)
         out["three_level"] = level_leg(mbs, stream, torch, "lambda_3lvl", 0, pk, clocks)
         if not args.no_batch:
-            out["batch"] = batch_leg(mbs, stream, torch, args.precision)
+            out["batch"] = batch_leg(mbs, stream, torch, "fp32")
         out["e2e"] = e2e(p, mbs, args, torch, stream)
         if world == 1 and not args.no_cpu:
             cb = time_oracle(p)
@@ -264,29 +277,30 @@ def level_leg(mbs, stream, torch, name, T, pk, clocks, reps=2, fp64_steps=1000):
     dev = mbs.device_from_problem(p)
     sc = mbs.scenario_from_problem(dev, p)
 
-    def timed(scn, prec, algo, tile):
-        mbs.mbs_solve([scn], prec, algo, tile_steps=tile, stream=stream.cuda_stream)   # warm-up
+    def timed(scn, prec, algo, tile, tune=False):
+        # warm-up (with tune: measures the tile depth, cached for the timed calls)
+        mbs.mbs_solve([scn], prec, algo, tile_steps=tile, stream=stream.cuda_stream, autotune=tune)
         torch.cuda.synchronize()
         best = None
         for _ in range(reps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            mbs.mbs_solve([scn], prec, algo, tile_steps=tile, stream=stream.cuda_stream)
+            mbs.mbs_solve([scn], prec, algo, tile_steps=tile, stream=stream.cuda_stream, autotune=tune)
             b.record(stream)
             torch.cuda.synchronize()
             t = a.elapsed_time(b) / 1e3
             best = t if best is None else min(best, t)
         return best
 
-    t = timed(sc, "fp32", "tiled", T)
+    t = timed(sc, "fp32", "tiled", T, tune=T == 0)
     launches = mbs.mbs_scenario_counters(sc)["kernel_launches"]
-    Teff = T if T else (24 if n == 2 else 32)
+    Teff = mbs.mbs_scenario_tile(sc)
     value = p.n_cells * p.n_steps / t / 1e9
     hbm = pk.get("hbm_gbs") or HBM_FALLBACK
     per_launch = t / max(1, launches)
     out = {"value": round(value, 3), "unit": METRIC,
            "workload": f"{p.name}: {p.n_cells} cells x {p.n_steps} steps, N={n}", "precision": "fp32",
-           "tile_steps": Teff}
+           "tile_steps": Teff, "tile_choice": "autotuned (MBS_SOLVE_AUTOTUNE)" if T == 0 else "fixed"}
     hb = {"bound": "hbm", "achieved": round(state_bytes(n) * value, 1), "peak": hbm, "unit": "GB/s",
           "frac": round(state_bytes(n) * value / hbm, 4), "alg_bytes_per_cell_step": state_bytes(n),
           "peak_source": "measured" if pk.get("hbm_gbs") else "fallback", "launch_ms": round(per_launch * 1e3, 5)}
@@ -326,33 +340,52 @@ def level_leg(mbs, stream, torch, name, T, pk, clocks, reps=2, fp64_steps=1000):
     return out
 
 
-def batch_leg(mbs, stream, torch, precision, T=0):
+def batch_leg(mbs, stream, torch, precision):
     """The 512-simulation mixed batch (two- and three-level media, 1,024 to
-    65,536 cells, 20,000 to 100,000 steps): one batched solve against the
-    same scenarios solved one after another (tile depth: the library's
-    default per level count unless T is given)."""
+    65,536 cells, 20,000 to 100,000 steps).  FP32: one batched solve with
+    autotuned tile depths, recorded as a CUDA graph on the warm-up call and
+    replayed on the timed call, against the same scenarios solved one after
+    another (library default depths).  FP64: one batched solve (default
+    depths, a single timed call)."""
     ps = W.batch_mixed()
     devs = [mbs.device_from_problem(p) for p in ps]
     scs = [mbs.scenario_from_problem(d, p) for d, p in zip(devs, ps)]
     cell_steps = sum(p.n_cells * p.n_steps for p in ps)
-    out = {}
-    for mode in ("batched", "one_at_a_time"):
-        one = mode == "one_at_a_time"
-        if not one:
-            mbs.mbs_solve(scs, precision, "tiled", tile_steps=T, stream=stream.cuda_stream)   # warm-up
+
+    def timed(**kw):
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        mbs.mbs_solve(scs, precision, "tiled", tile_steps=T, stream=stream.cuda_stream, one_at_a_time=one)
+        mbs.mbs_solve(scs, stream=stream.cuda_stream, **kw)
         b.record(stream)
         torch.cuda.synchronize()
-        out[mode] = cell_steps / (a.elapsed_time(b) / 1e3) / 1e9
+        return cell_steps / (a.elapsed_time(b) / 1e3) / 1e9
+
+    kw32 = dict(precision="fp32", algo="tiled", autotune=True, graph=True)
+    timed(**kw32)                                                       # tunes, records the graph
+    batched = timed(**kw32)                                             # replays it
+    tiles = sorted({(p.qms[0].n_levels, mbs.mbs_scenario_tile(sc)) for p, sc in zip(ps, scs)})
+    one = timed(precision="fp32", algo="tiled", one_at_a_time=True)
+    # FP64 and FP32 batched on the first 64 simulations (a bounded sample)
+    sub, sub_ps = scs[:64], ps[:64]
+    sub_cs = sum(p.n_cells * p.n_steps for p in sub_ps)
+    rate = {}
+    for prec in ("fp64", "fp32"):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mbs.mbs_solve(sub, prec, "tiled", stream=stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        rate[prec] = sub_cs / (a.elapsed_time(b) / 1e3) / 1e9
     n2 = sum(1 for p in ps if p.qms[0].n_levels == 2)
-    return {"value": round(out["batched"], 2), "one_at_a_time": round(out["one_at_a_time"], 2),
-            "speedup": round(out["batched"] / out["one_at_a_time"], 2), "unit": METRIC,
+    return {"value": round(batched, 2), "one_at_a_time": round(one, 2), "speedup": round(batched / one, 2),
+            "fp64_batched": {"value": round(rate["fp64"], 2), "fp32_same_sample": round(rate["fp32"], 2),
+                             "sample": f"first 64 simulations, {sub_cs:.3e} cell-steps, default tile depths"},
+            "unit": METRIC,
             "workload": f"{len(ps)} simulations ({n2} two-level, {len(ps) - n2} three-level), "
                         f"{cell_steps:.3e} cell-steps", "precision": precision,
-            "tile_steps": T if T else "library default (24 two-level, 32 three-level)"}
+            "tile_steps": {f"N={n}": t for n, t in tiles}, "launch": "CUDA graph replay (MBS_SOLVE_GRAPH)"}
 
 
 def fp64_plain(p, mbs, stream, torch, steps=4000):

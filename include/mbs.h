@@ -156,12 +156,27 @@ enum { MBS_ALGO_AUTO = 0,
                                   with halo recompute (the redundant-calculation
                                   loop of Sec. 3.2) */
 
-enum { MBS_SOLVE_ONE_AT_A_TIME = 1 };  /* flags: solve batch members one after another */
+enum { MBS_SOLVE_ONE_AT_A_TIME = 1,  /* flags: solve batch members one after another */
+       MBS_SOLVE_AUTOTUNE = 2,       /* with tile_steps == 0: pick the tile depth by measurement.
+                                        Each candidate depth runs one warm-up and three timed
+                                        launches (CUDA events on cuda_stream) from the current
+                                        state, which is then reset; the fastest per step wins.
+                                        The choice is cached for the process per level count,
+                                        precision, kernel variant and cell / step counts (per
+                                        batch group: its simulations' totals). */
+       MBS_SOLVE_GRAPH = 4 };        /* batched tiled solves on a non-NULL stream: the first call
+                                        records the whole launch sequence (fork, every round of
+                                        every group, join, state checks) into a CUDA graph and
+                                        launches it; later calls with the same scenarios (same
+                                        order) and options replay it without rebuilding the task
+                                        tables.  Destroying a member scenario frees the graph. */
 
 typedef struct {
     int precision;     /* MBS_PREC_* */
     int algo;          /* MBS_ALGO_* */
-    int tile_steps;    /* steps per tiled launch (multiple of 4), 0 = default (24 for two levels, 32 for three) */
+    int tile_steps;    /* steps per tiled launch: N = 2, 3 a multiple of 4 in [4, 32R - 12] (R = 4 cells per
+                          lane for N = 2, 2 for N = 3); N >= 4 in [1, 20].  0 = the library's choice:
+                          measured with MBS_SOLVE_AUTOTUNE, else 24 (N = 2), 32 (N = 3), 8 (N >= 4) */
     int check_every;   /* steps between device-side state checks, 0 = only at the end */
     int flags;         /* MBS_SOLVE_* */
 } mbs_opts;
@@ -213,6 +228,10 @@ int mbs_scenario_stats(mbs_scenario_t s, double *max_trace_dev, double *min_eig,
 int mbs_device_propagators(mbs_device_t dev, int qm, double dt,
                            double *lambda, double *V, double *A, double *Ah,
                            double *c, double *zref, double *g, double *g0);
+
+/* Tile depth (steps per tiled launch) the last solve used, 0 for the plain
+ * path; MBS_E_STATE before the first solve. */
+int mbs_scenario_tile(mbs_scenario_t s, int *tile_steps);
 
 /* Transfer and launch counters: bytes copied host -> device by the
  * scenario's creation and its solves so far, bytes copied device -> host by

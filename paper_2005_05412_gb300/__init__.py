@@ -71,7 +71,7 @@ class _Opts(C.Structure):
                 ("flags", C.c_int)]
 
 
-MBS_SOLVE_ONE_AT_A_TIME = 1
+MBS_SOLVE_ONE_AT_A_TIME, MBS_SOLVE_AUTOTUNE, MBS_SOLVE_GRAPH = 1, 2, 4
 
 
 _lib = None
@@ -79,7 +79,7 @@ _lib = None
 # every symbol include/mbs.h declares
 EXPORTS = ["mbs_device_create", "mbs_device_destroy", "mbs_device_propagators", "mbs_scenario",
            "mbs_scenario_destroy", "mbs_scenario_info", "mbs_scenario_stats", "mbs_scenario_counters", "mbs_solve",
-           "mbs_fetch_records", "mbs_last_error", "mbs_abi_version", "mbs_check_rho_static"]
+           "mbs_fetch_records", "mbs_last_error", "mbs_abi_version", "mbs_check_rho_static", "mbs_scenario_tile"]
 
 
 def lib():
@@ -101,6 +101,7 @@ def lib():
         L.mbs_scenario_info.argtypes = [vp, C.POINTER(d), C.POINTER(d), C.POINTER(ll)]
         L.mbs_scenario_stats.argtypes = [vp, C.POINTER(d), C.POINTER(d), C.POINTER(ll)]
         L.mbs_scenario_counters.argtypes = [vp, C.POINTER(ll), C.POINTER(ll), C.POINTER(ll)]
+        L.mbs_scenario_tile.argtypes = [vp, C.POINTER(i)]
         L.mbs_solve.argtypes = [C.POINTER(vp), i, C.POINTER(_Opts), vp]
         L.mbs_fetch_records.argtypes = [vp, i, vp, C.c_size_t, C.POINTER(C.c_size_t)]
         L.mbs_last_error.restype = C.c_char_p
@@ -212,16 +213,18 @@ def mbs_scenario(device: Device, dt=0.0, courant=1.0, t_end=0.0, n_steps=0, sour
 
 
 def mbs_solve(scenarios, precision="fp32", algo="auto", tile_steps=0, check_every=0, stream=None,
-              one_at_a_time=False):
+              one_at_a_time=False, autotune=False, graph=False):
     """Run every scenario to its end (a batch advances together unless
     one_at_a_time).  stream: a cudaStream_t handle (int), e.g.
-    torch.cuda.current_stream().cuda_stream, or None."""
+    torch.cuda.current_stream().cuda_stream, or None.  autotune / graph set
+    MBS_SOLVE_AUTOTUNE / MBS_SOLVE_GRAPH (see include/mbs.h)."""
     if isinstance(scenarios, Scenario):
         scenarios = [scenarios]
     arr = (C.c_void_p * len(scenarios))(*[s.handle for s in scenarios])
+    flags = ((MBS_SOLVE_ONE_AT_A_TIME if one_at_a_time else 0) | (MBS_SOLVE_AUTOTUNE if autotune else 0)
+             | (MBS_SOLVE_GRAPH if graph else 0))
     o = _Opts(PREC[precision] if isinstance(precision, str) else int(precision),
-              ALGO[algo] if isinstance(algo, str) else int(algo), int(tile_steps), int(check_every),
-              MBS_SOLVE_ONE_AT_A_TIME if one_at_a_time else 0)
+              ALGO[algo] if isinstance(algo, str) else int(algo), int(tile_steps), int(check_every), flags)
     return _check(lib().mbs_solve(arr, len(scenarios), C.byref(o), None if stream is None else C.c_void_p(int(stream))))
 
 
@@ -245,6 +248,12 @@ def mbs_scenario_stats(scenario: Scenario):
     tr, mn, nt = C.c_double(), C.c_double(), C.c_longlong()
     _check(lib().mbs_scenario_stats(scenario.handle, C.byref(tr), C.byref(mn), C.byref(nt)))
     return dict(max_trace_dev=tr.value, min_eig=mn.value, n_steps=nt.value)
+
+
+def mbs_scenario_tile(scenario: Scenario) -> int:
+    t = C.c_int()
+    _check(lib().mbs_scenario_tile(scenario.handle, C.byref(t)))
+    return t.value
 
 
 def mbs_scenario_counters(scenario: Scenario):

@@ -20,12 +20,15 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <climits>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 #ifdef _OPENMP
@@ -417,11 +420,14 @@ struct mbs_scenario_s {
   std::vector<int> chk_cells;
   Bundle b[2];
   int solved_prec = -1, last_cur = 0;
+  int tile_used = 0;   // tile depth of the last solve (0: plain path)
   long long h2d_bytes = 0, d2h_bytes = 0, launches = 0;
   long long steps_run = 0;
   double st_trace = 0, st_min = 0;
   int device_id = 0;
 };
+
+static void drop_graphs_of(mbs_scenario_s *s);   // batched-solve graphs that use s
 
 namespace {
 
@@ -1150,6 +1156,7 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
 
 void mbs_scenario_destroy(mbs_scenario_t s) {
   if (!s) return;
+  drop_graphs_of(s);
   free_scenario(s);
   delete s;
 }
@@ -1270,21 +1277,103 @@ static int finish_solve(mbs_scenario_s *s, int prec, int cur) {
   return MBS_OK;
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------ autotuning
+// Tile depth by measurement: every candidate depth runs one warm-up launch and
+// three timed launches (CUDA events on the solve stream) of the scenario (or
+// of the whole batch group) from its current state; the fastest time per step
+// wins.  The caller resets the state afterwards.  Results are cached for the
+// process, keyed by level count, precision, kernel variant and the cell and
+// step counts, so a workload shape is tuned once.
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune;
+
+static std::vector<int> tile_candidates(int N, long long nt) {
+  std::vector<int> c = N >= 4 ? std::vector<int>{6, 8, 10, 12, 14, 16, 20}
+                     : N == 3 ? std::vector<int>{16, 20, 24, 28, 32, 40, 48}
+                              : std::vector<int>{12, 16, 20, 24, 28, 32, 40, 48};
+  std::vector<int> out;
+  for (int T : c)
+    if (T <= nt) out.push_back(T);
+  return out;
+}
+
+static int tiled_launch(const mbs_scenario_s *s, const mbs::Args &a, long long n0, int ns, int T, int cur,
+                        cudaStream_t st) {
+  return s->N >= 4 ? mbs::launch_tiled_tc(a, n0, ns, T, cur, st) : mbs::launch_tiled(a, n0, ns, T, cur, st);
+}
+
+// time `run(T)` (which enqueues one launch) for every candidate; -1 on error
+template <class Run>
+static int tune_loop(const std::vector<int> &cands, cudaStream_t st, Run run) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return -1;
+  }
+  int best = -1;
+  float best_t = FLT_MAX;
+  for (int T : cands) {
+    bool ok = run(T, 0) == 0;
+    ok = ok && cudaEventRecord(e0, st) == cudaSuccess;
+    for (int r = 0; r < 3 && ok; ++r) ok = run(T, (r + 1) & 1) == 0;
+    ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+    float ms = 0;
+    if (!ok || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      best = -1;
+      break;
+    }
+    const float per_step = ms / (3.0f * T);
+    if (per_step < best_t) {
+      best_t = per_step;
+      best = T;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+static int autotune_one(mbs_scenario_s *s, int prec, const mbs::Args &a, cudaStream_t st) {
+  char key[128];
+  std::snprintf(key, sizeof key, "1:%d:%d:%d:%d:%d", s->N, prec, s->N >= 4 ? 9 : mbs::tiled_variant(a), s->dev->nx,
+                (int)std::min<long long>(s->nt, 1 << 30));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  std::vector<int> cands;
+  for (int T : tile_candidates(s->N, s->nt))
+    if (s->N >= 4 ? T <= mbs::tiled_tc_max_steps() : T <= mbs::tile_max_steps(s->N)) cands.push_back(T);
+  if (cands.size() < 2) return default_tile_steps(s->N);
+  const int T = tune_loop(cands, st, [&](int t, int cur) { return tiled_launch(s, a, 0, t, t, cur, st); });
+  if (T < 0) return default_tile_steps(s->N);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = T;
+  return T;
+}
+
 static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
   const int prec = o.precision;
   int rc = prepare_solve(s, prec, st);
   if (rc) return rc;
   mbs::Args a = make_args(s, prec);
   int algo = o.algo == MBS_ALGO_AUTO ? default_algo(s, prec) : o.algo;
-  const int T = o.tile_steps > 0 ? o.tile_steps : default_tile_steps(s->N);
+  int T = o.tile_steps > 0 ? o.tile_steps : default_tile_steps(s->N);
   const int chk = o.check_every > 0 ? o.check_every : 0;
   int cur = 0;
   if (algo == MBS_ALGO_TILED) {
     if ((rc = tiled_ok(s, prec, T))) return rc;
+    if (o.tile_steps <= 0 && (o.flags & MBS_SOLVE_AUTOTUNE)) {
+      T = autotune_one(s, prec, a, st);
+      if ((rc = prepare_solve(s, prec, st))) return rc;   // the trials advanced the state
+    }
     long long done = 0;
     while (done < s->nt) {
       const int ns = (int)std::min<long long>(T, s->nt - done);
-      int r = s->N >= 4 ? mbs::launch_tiled_tc(a, done, ns, T, cur, st) : mbs::launch_tiled(a, done, ns, T, cur, st);
+      int r = tiled_launch(s, a, done, ns, T, cur, st);
       ++s->launches;
       if (r) return cuda_fail((cudaError_t)r, "tiled launch");
       cur ^= 1;
@@ -1292,6 +1381,7 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
       if (chk && done < s->nt && (done / chk) != ((done - ns) / chk))
         if ((r = launch_state_check(s, a, cur, st))) return cuda_fail((cudaError_t)r, "check launch");
     }
+    s->tile_used = T;
   } else {
     for (long long n = 0; n < s->nt; ++n) {
       int r = mbs::launch_plain_step(a, n, cur, st);
@@ -1301,6 +1391,7 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
       if (chk && (n + 1) % chk == 0 && n + 1 < s->nt)
         if ((r = launch_state_check(s, a, 0, st))) return cuda_fail((cudaError_t)r, "check launch");
     }
+    s->tile_used = 0;
   }
   // plain: D, H live in buffer 0, E in `cur`; tiled: everything in `cur`
   const int dcur = algo == MBS_ALGO_TILED ? cur : 0;
@@ -1314,6 +1405,63 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
 // over the blocks of all simulations still running, advancing them T steps.
 // Blocks are ordered by their simulation's step count (longest first), so
 // the running ones form a prefix and the grid shrinks as simulations end.
+struct BatchGroup {
+  int N, pm, T;
+  std::vector<int> sims;   // indices into the batch, longest first
+  std::vector<int2> tasks;
+  std::vector<long long> task_nt;
+  int max_mat = 0, max_slot = 0, max_stride = 0;
+};
+
+static void group_tasks(BatchGroup &g, const std::vector<mbs_scenario_s *> &ss, int T,
+                        std::vector<int2> &tasks, std::vector<long long> &task_nt) {
+  tasks.clear();
+  task_nt.clear();
+  const int own = mbs::tile_own(g.N, T);
+  for (int i : g.sims) {
+    const int n_tiles = (ss[i]->dev->nx + own - 1) / own;
+    for (int w = 0; w < n_tiles; ++w) {
+      tasks.push_back(make_int2(i, w));
+      task_nt.push_back(ss[i]->nt);
+    }
+  }
+}
+
+// A batched solve recorded as a CUDA graph (MBS_SOLVE_GRAPH), with the device
+// tables its launches read; replayed while the same scenarios are solved with
+// the same options.  Destroying a member scenario drops the graph.
+struct BatchGraph {
+  std::vector<mbs_scenario_s *> members;
+  int prec = 0, tile = 0, flags = 0;
+  std::vector<int> Ts;      // tile depth per group
+  std::vector<int> sim_T;   // tile depth per member
+  cudaGraphExec_t exec = nullptr;
+  mbs::Args *d_args = nullptr;
+  std::vector<int2 *> d_tasks;
+};
+static std::mutex g_graph_mu;
+static std::vector<BatchGraph *> g_graphs;
+
+static void free_graph(BatchGraph *g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  cudaFree(g->d_args);
+  for (auto *p : g->d_tasks) cudaFree(p);
+  delete g;
+}
+
+static void drop_graphs_of(mbs_scenario_s *s) {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  for (size_t k = 0; k < g_graphs.size();) {
+    auto &m = g_graphs[k]->members;
+    if (std::find(m.begin(), m.end(), s) != m.end()) {
+      free_graph(g_graphs[k]);
+      g_graphs.erase(g_graphs.begin() + k);
+    } else {
+      ++k;
+    }
+  }
+}
+
 static int solve_batch(std::vector<mbs_scenario_s *> &ss, const mbs_opts &o, cudaStream_t st) {
   const int prec = o.precision;
   int rc;
@@ -1321,24 +1469,39 @@ static int solve_batch(std::vector<mbs_scenario_s *> &ss, const mbs_opts &o, cud
     if ((rc = prepare_solve(s, prec, st))) return rc;
     if ((rc = tiled_ok(s, prec, o.tile_steps > 0 ? o.tile_steps : default_tile_steps(s->N)))) return rc;
   }
-  struct Group {
-    int N, pm, T;
-    std::vector<int> sims;        // indices into ss, longest first
-    std::vector<int2> tasks;
-    std::vector<long long> task_nt;
-    int max_mat = 0, max_slot = 0, max_stride = 0;
-  };
-  std::vector<Group> groups;
+  // graphs need a stream that can be captured (not the legacy default stream)
+  const bool use_graph = (o.flags & MBS_SOLVE_GRAPH) != 0 && st != nullptr;
+  // replay a recorded graph of this very batch
+  if (use_graph) {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto *g : g_graphs)
+      if (g->members == ss && g->prec == prec && g->tile == o.tile_steps && g->flags == o.flags) {
+        cudaError_t e = cudaGraphLaunch(g->exec, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "batched graph replay");
+        int status = MBS_OK;
+        for (size_t i = 0; i < ss.size(); ++i) {
+          const int T = g->sim_T[i];
+          const long long rounds = (ss[i]->nt + T - 1) / T;
+          ss[i]->launches = rounds;
+          ss[i]->tile_used = T;
+          rc = finish_solve(ss[i], prec, (int)(rounds % 2));
+          if (rc && status == MBS_OK) status = rc;
+        }
+        return status;
+      }
+  }
+  std::vector<BatchGroup> groups;
   std::vector<mbs::Args> args(ss.size());
   for (size_t i = 0; i < ss.size(); ++i) {
     args[i] = make_args(ss[i], prec);
     const int pm = mbs::tiled_variant(args[i]);
     if (pm < 0) return fail(MBS_E_INVALID, "scenario %zu is not covered by the tiled kernels", i);
-    Group *g = nullptr;
+    BatchGroup *g = nullptr;
     for (auto &x : groups)
       if (x.N == ss[i]->N && x.pm == pm) g = &x;
     if (!g) {
-      groups.push_back(Group{ss[i]->N, pm, o.tile_steps > 0 ? o.tile_steps : default_tile_steps(ss[i]->N)});
+      groups.push_back(BatchGroup{ss[i]->N, pm, o.tile_steps > 0 ? o.tile_steps : default_tile_steps(ss[i]->N)});
       g = &groups.back();
     }
     g->sims.push_back((int)i);
@@ -1346,36 +1509,88 @@ static int solve_batch(std::vector<mbs_scenario_s *> &ss, const mbs_opts &o, cud
     g->max_slot = std::max(g->max_slot, args[i].n_slot);
     g->max_stride = std::max(g->max_stride, args[i].qstride);
   }
-  for (auto &g : groups) {
+  for (auto &g : groups)
     std::stable_sort(g.sims.begin(), g.sims.end(), [&](int x, int y) { return ss[x]->nt > ss[y]->nt; });
-    const int own = mbs::tile_own(g.N, g.T);
-    for (int i : g.sims) {
-      const int n_tiles = (ss[i]->dev->nx + own - 1) / own;
-      for (int w = 0; w < n_tiles; ++w) {
-        g.tasks.push_back(make_int2(i, w));
-        g.task_nt.push_back(ss[i]->nt);
-      }
-    }
-  }
-  // device copies of the per-simulation arguments and the block tasks
+  // device copy of the per-simulation arguments
   mbs::Args *d_args = nullptr;
   std::vector<int2 *> d_tasks(groups.size(), nullptr);
+  auto cleanup = [&]() {
+    cudaFree(d_args);
+    for (auto *p : d_tasks) cudaFree(p);
+  };
   cudaError_t e = cudaMalloc(&d_args, args.size() * sizeof(mbs::Args));
   if (e == cudaSuccess) e = cudaMemcpy(d_args, args.data(), args.size() * sizeof(mbs::Args), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "batch tables");
+  }
+  // tile depth per group: given, default, or measured
+  if (o.tile_steps <= 0 && (o.flags & MBS_SOLVE_AUTOTUNE)) {
+    for (auto &g : groups) {
+      long long nt_min = LLONG_MAX, cells = 0, steps = 0;
+      for (int i : g.sims) {
+        nt_min = std::min(nt_min, ss[i]->nt);
+        cells += ss[i]->dev->nx;
+        steps += ss[i]->nt;
+      }
+      char key[160];
+      std::snprintf(key, sizeof key, "B:%d:%d:%d:%zu:%lld:%lld", g.N, prec, g.pm, g.sims.size(), cells, steps);
+      int T = -1;
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) T = it->second;
+      }
+      if (T < 0) {
+        std::vector<int> cands;
+        for (int t : tile_candidates(g.N, nt_min))
+          if (t <= mbs::tile_max_steps(g.N)) cands.push_back(t);
+        const size_t smem = mbs::tiled_batch_smem(prec, g.N, g.max_mat, g.max_slot, g.max_stride);
+        std::vector<int2> tk;
+        std::vector<long long> tn;
+        int2 *d_tk = nullptr;
+        int last_T = -1;
+        T = tune_loop(cands, st, [&](int t, int cur) {
+          if (t != last_T) {   // tasks of this depth
+            if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+            cudaFree(d_tk);
+            d_tk = nullptr;
+            group_tasks(g, ss, t, tk, tn);
+            if (cudaMalloc(&d_tk, tk.size() * sizeof(int2)) != cudaSuccess ||
+                cudaMemcpy(d_tk, tk.data(), tk.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+              return -1;
+            last_T = t;
+          }
+          return mbs::launch_tiled_batch(prec, g.N, g.pm, d_args, d_tk, (int)tk.size(), smem, 0, t, cur, st);
+        });
+        cudaStreamSynchronize(st);
+        cudaFree(d_tk);
+        if (T < 0) T = default_tile_steps(g.N);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = T;
+      }
+      g.T = T;
+    }
+    for (auto *s : ss)   // the trials advanced the state
+      if ((rc = prepare_solve(s, prec, st))) {
+        cleanup();
+        return rc;
+      }
+  }
   for (size_t k = 0; k < groups.size() && e == cudaSuccess; ++k) {
+    group_tasks(groups[k], ss, groups[k].T, groups[k].tasks, groups[k].task_nt);
     e = cudaMalloc(&d_tasks[k], groups[k].tasks.size() * sizeof(int2));
     if (e == cudaSuccess)
       e = cudaMemcpy(d_tasks[k], groups[k].tasks.data(), groups[k].tasks.size() * sizeof(int2),
                      cudaMemcpyHostToDevice);
   }
-  auto cleanup = [&]() {
-    cudaFree(d_args);
-    for (auto *p : d_tasks) cudaFree(p);
-  };
   if (e != cudaSuccess) {
     cleanup();
     return cuda_fail(e, "batch tables");
   }
+  std::vector<int> sim_T(ss.size());
+  for (const auto &g : groups)
+    for (int i : g.sims) sim_T[i] = g.T;
   // Each group runs on a stream of its own, forked from and joined back into
   // the caller's stream, so that one group's last, thinly populated rounds
   // overlap the other group's work.
@@ -1394,71 +1609,107 @@ static int solve_batch(std::vector<mbs_scenario_s *> &ss, const mbs_opts &o, cud
   }
   for (size_t k = 0; k < ev.size() && n_fork && e == cudaSuccess; ++k)
     e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
-  if (n_fork && e == cudaSuccess) e = cudaEventRecord(ev[n_fork], st);
-  for (size_t k = 0; k < n_fork && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(gst[k], ev[n_fork], 0);
   if (e != cudaSuccess) {
     release();
     cleanup();
     return cuda_fail(e, "batch streams");
   }
-  for (size_t k = 0; k < groups.size(); ++k) {
-    const auto &g = groups[k];
-    const size_t smem = mbs::tiled_batch_smem(prec, g.N, g.max_mat, g.max_slot, g.max_stride);
-    const long long nt_max = g.task_nt.front();
-    int cur = 0;
-    for (long long n0 = 0; n0 < nt_max; n0 += g.T) {
-      // running blocks: a prefix of the tasks (sorted by step count)
-      const int active = (int)(std::upper_bound(g.task_nt.begin(), g.task_nt.end(), n0,
-                                                [](long long v, long long x) { return v > x; }) -
-                               g.task_nt.begin());
-      const int r =
-          mbs::launch_tiled_batch(prec, g.N, g.pm, d_args, d_tasks[k], active, smem, n0, g.T, cur, gst[k]);
-      if (r) {
-        release();
-        cleanup();
-        return cuda_fail((cudaError_t)r, "batched tiled launch");
+  // the launch sequence: fork, every group's rounds, join, per-simulation checks
+  auto enqueue = [&]() -> int {
+    cudaError_t x = cudaSuccess;
+    if (n_fork) x = cudaEventRecord(ev[n_fork], st);
+    for (size_t k = 0; k < n_fork && x == cudaSuccess; ++k) x = cudaStreamWaitEvent(gst[k], ev[n_fork], 0);
+    if (x != cudaSuccess) return cuda_fail(x, "batch streams");
+    for (size_t k = 0; k < groups.size(); ++k) {
+      const auto &g = groups[k];
+      const size_t smem = mbs::tiled_batch_smem(prec, g.N, g.max_mat, g.max_slot, g.max_stride);
+      const long long nt_max = g.task_nt.front();
+      int cur = 0;
+      for (long long n0 = 0; n0 < nt_max; n0 += g.T) {
+        // running blocks: a prefix of the tasks (sorted by step count)
+        const int active = (int)(std::upper_bound(g.task_nt.begin(), g.task_nt.end(), n0,
+                                                  [](long long v, long long y) { return v > y; }) -
+                                 g.task_nt.begin());
+        const int r =
+            mbs::launch_tiled_batch(prec, g.N, g.pm, d_args, d_tasks[k], active, smem, n0, g.T, cur, gst[k]);
+        if (r) return cuda_fail((cudaError_t)r, "batched tiled launch");
+        cur ^= 1;
       }
-      cur ^= 1;
     }
-  }
-  for (size_t k = 0; k < n_fork && e == cudaSuccess; ++k) {
-    e = cudaEventRecord(ev[k], gst[k]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[k], 0);
-  }
-  if (e != cudaSuccess) {
-    release();
-    cleanup();
-    return cuda_fail(e, "batch streams");
-  }
-  // final state check of every simulation in its own final buffer
-  std::vector<int> sim_T(ss.size());
-  for (const auto &g : groups)
-    for (int i : g.sims) sim_T[i] = g.T;
-  for (size_t i = 0; i < ss.size(); ++i) {
-    auto *s = ss[i];
-    const int T = sim_T[i];
-    const long long rounds = (s->nt + T - 1) / T;
-    s->launches = rounds;
-    if ((rc = launch_state_check(s, args[i], (int)(rounds % 2), st))) {
+    for (size_t k = 0; k < n_fork && x == cudaSuccess; ++k) {
+      x = cudaEventRecord(ev[k], gst[k]);
+      if (x == cudaSuccess) x = cudaStreamWaitEvent(st, ev[k], 0);
+    }
+    if (x != cudaSuccess) return cuda_fail(x, "batch streams");
+    for (size_t i = 0; i < ss.size(); ++i) {
+      const long long rounds = (ss[i]->nt + sim_T[i] - 1) / sim_T[i];
+      const int r = launch_state_check(ss[i], args[i], (int)(rounds % 2), st);
+      if (r) return cuda_fail((cudaError_t)r, "check launch");
+    }
+    return MBS_OK;
+  };
+  BatchGraph *graph = nullptr;
+  if (use_graph) {
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      release();
+      cleanup();
+      return cuda_fail(e, "graph capture (a NULL or legacy stream cannot be captured)");
+    }
+    rc = enqueue();
+    const cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+    if (rc == MBS_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "graph capture");
+    graph = new BatchGraph;
+    if (rc == MBS_OK && (e = cudaGraphInstantiate(&graph->exec, gr, 0)) != cudaSuccess)
+      rc = cuda_fail(e, "graph instantiation");
+    if (gr) cudaGraphDestroy(gr);
+    if (rc == MBS_OK && (e = cudaGraphLaunch(graph->exec, st)) != cudaSuccess) rc = cuda_fail(e, "graph launch");
+    if (rc != MBS_OK) {
+      free_graph(graph);
+      release();
+      cleanup();
+      return rc;
+    }
+  } else {
+    rc = enqueue();
+    if (rc != MBS_OK) {
       cudaStreamSynchronize(st);
       release();
       cleanup();
-      return cuda_fail((cudaError_t)rc, "check launch");
+      return rc;
     }
   }
   e = cudaStreamSynchronize(st);
   release();
-  cleanup();
+  if (graph) {   // the graph keeps the tables it reads
+    graph->members = ss;
+    graph->prec = prec;
+    graph->tile = o.tile_steps;
+    graph->flags = o.flags;
+    for (const auto &g : groups) graph->Ts.push_back(g.T);
+    graph->sim_T = sim_T;
+    graph->d_args = d_args;
+    graph->d_tasks = d_tasks;
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    g_graphs.push_back(graph);
+  } else {
+    cleanup();
+  }
   if (e != cudaSuccess) return cuda_fail(e, "batched solve");
   int status = MBS_OK;
   for (size_t i = 0; i < ss.size(); ++i) {
     auto *s = ss[i];
     const long long rounds = (s->nt + sim_T[i] - 1) / sim_T[i];
+    s->launches = rounds;
+    s->tile_used = sim_T[i];
     rc = finish_solve(s, prec, (int)(rounds % 2));
     if (rc && status == MBS_OK) status = rc;
   }
   return status;
 }
+
+extern "C" {
 
 int mbs_solve(mbs_scenario_t *batch, int n_scen, const mbs_opts *opts, void *cuda_stream) {
   g_err.clear();
@@ -1511,6 +1762,14 @@ int mbs_fetch_records(mbs_scenario_t s, int probe, double *out, size_t cap, size
     s->d2h_bytes += (long long)(n * sizeof(float));
     for (size_t i = 0; i < n; ++i) out[i] = scale * (double)f[i];
   }
+  return MBS_OK;
+}
+
+int mbs_scenario_tile(mbs_scenario_t s, int *tile_steps) {
+  g_err.clear();
+  if (!s) return fail(MBS_E_INVALID, "scenario is NULL");
+  if (s->solved_prec < 0) return fail(MBS_E_STATE, "no solve has run");
+  if (tile_steps) *tile_steps = s->tile_used;
   return MBS_OK;
 }
 
