@@ -170,13 +170,19 @@ enum { MBS_SOLVE_ONE_AT_A_TIME = 1,  /* flags: solve batch members one after ano
                                         launches it; later calls with the same scenarios (same
                                         order) and options replay it without rebuilding the task
                                         tables.  Destroying a member scenario frees the graph. */
+enum { MBS_SOLVE_WIDE_TILES = 8 };   /* N >= 4: tensor-core tiles of 256 cells (two 128-row MMA
+                                        groups per block) instead of 128; tile_steps must keep the
+                                        absorbing ends inside a tile's light cone for the grid
+                                        (always true for 1..26) */
 
 typedef struct {
     int precision;     /* MBS_PREC_* */
     int algo;          /* MBS_ALGO_* */
     int tile_steps;    /* steps per tiled launch: N = 2, 3 a multiple of 4 in [4, 32R - 12] (R = 4 cells per
-                          lane for N = 2, 2 for N = 3); N >= 4 in [1, 20].  0 = the library's choice:
-                          measured with MBS_SOLVE_AUTOTUNE, else 24 (N = 2), 32 (N = 3), 8 (N >= 4) */
+                          lane for N = 2, 2 for N = 3); N >= 4 in [1, 20] (128-cell tiles) or
+                          [1, 26] (256-cell tiles; other depths are checked against the grid).
+                          0 = the library's choice: measured with MBS_SOLVE_AUTOTUNE (for N >= 4
+                          also the tile width), else 24 (N = 2), 32 (N = 3), 8 / 20 (N >= 4) */
     int check_every;   /* steps between device-side state checks, 0 = only at the end */
     int flags;         /* MBS_SOLVE_* */
 } mbs_opts;

@@ -71,7 +71,7 @@ class _Opts(C.Structure):
                 ("flags", C.c_int)]
 
 
-MBS_SOLVE_ONE_AT_A_TIME, MBS_SOLVE_AUTOTUNE, MBS_SOLVE_GRAPH = 1, 2, 4
+MBS_SOLVE_ONE_AT_A_TIME, MBS_SOLVE_AUTOTUNE, MBS_SOLVE_GRAPH, MBS_SOLVE_WIDE_TILES = 1, 2, 4, 8
 
 
 _lib = None
@@ -213,16 +213,17 @@ def mbs_scenario(device: Device, dt=0.0, courant=1.0, t_end=0.0, n_steps=0, sour
 
 
 def mbs_solve(scenarios, precision="fp32", algo="auto", tile_steps=0, check_every=0, stream=None,
-              one_at_a_time=False, autotune=False, graph=False):
+              one_at_a_time=False, autotune=False, graph=False, wide_tiles=False):
     """Run every scenario to its end (a batch advances together unless
     one_at_a_time).  stream: a cudaStream_t handle (int), e.g.
-    torch.cuda.current_stream().cuda_stream, or None.  autotune / graph set
-    MBS_SOLVE_AUTOTUNE / MBS_SOLVE_GRAPH (see include/mbs.h)."""
+    torch.cuda.current_stream().cuda_stream, or None.  autotune / graph /
+    wide_tiles set MBS_SOLVE_AUTOTUNE / MBS_SOLVE_GRAPH / MBS_SOLVE_WIDE_TILES
+    (see include/mbs.h)."""
     if isinstance(scenarios, Scenario):
         scenarios = [scenarios]
     arr = (C.c_void_p * len(scenarios))(*[s.handle for s in scenarios])
     flags = ((MBS_SOLVE_ONE_AT_A_TIME if one_at_a_time else 0) | (MBS_SOLVE_AUTOTUNE if autotune else 0)
-             | (MBS_SOLVE_GRAPH if graph else 0))
+             | (MBS_SOLVE_GRAPH if graph else 0) | (MBS_SOLVE_WIDE_TILES if wide_tiles else 0))
     o = _Opts(PREC[precision] if isinstance(precision, str) else int(precision),
               ALGO[algo] if isinstance(algo, str) else int(algo), int(tile_steps), int(check_every), flags)
     return _check(lib().mbs_solve(arr, len(scenarios), C.byref(o), None if stream is None else C.c_void_p(int(stream))))
@@ -300,12 +301,12 @@ def scenario_from_problem(dev: Device, p, courant=None) -> Scenario:
                         p.sources, p.probes)
 
 
-def run(p, precision="fp32", algo="auto", tile_steps=0, check_every=0, stream=None):
+def run(p, precision="fp32", algo="auto", tile_steps=0, check_every=0, stream=None, **flags):
     """Create, solve and fetch one problem; returns dict(records, dt, nt,
     stats, counters, device_status)."""
     dev = device_from_problem(p)
     sc = scenario_from_problem(dev, p)
-    mbs_solve([sc], precision, algo, tile_steps, check_every, stream)
+    mbs_solve([sc], precision, algo, tile_steps, check_every, stream, **flags)
     dt, dz, nt = mbs_scenario_info(sc)
     rec = np.stack([mbs_fetch_records(sc, k) for k in range(len(p.probes))]) if p.probes else np.zeros((0, nt))
     return dict(records=rec, dt=dt, nt=nt, stats=mbs_scenario_stats(sc), counters=mbs_scenario_counters(sc),

@@ -421,6 +421,7 @@ struct mbs_scenario_s {
   Bundle b[2];
   int solved_prec = -1, last_cur = 0;
   int tile_used = 0;   // tile depth of the last solve (0: plain path)
+  int tc_cells = 128;  // cells per tensor-core tile of the current solve (N >= 4)
   long long h2d_bytes = 0, d2h_bytes = 0, launches = 0;
   long long steps_run = 0;
   double st_trace = 0, st_min = 0;
@@ -1197,8 +1198,9 @@ static int prepare_solve(mbs_scenario_s *s, int prec, cudaStream_t st) {
 }
 
 // Tile depth when the caller leaves it to the library: the fastest measured
-// on GB300 (two levels: 24 steps, three levels: 32, tensor-core tiles: 8).
-static int default_tile_steps(int N) { return N == 2 ? 24 : N == 3 ? 32 : 8; }
+// on GB300 (two levels: 24 steps, three levels: 32, tensor-core tiles: 8 for
+// 128 cells, 20 for 256 cells).
+static int default_tile_steps(int N, int tc_cells = 128) { return N == 2 ? 24 : N == 3 ? 32 : tc_cells == 256 ? 20 : 8; }
 
 // Whether scenario s runs on the tensor-core tiles (N = 4..6 in FP32 with a
 // single medium and no per-cell operators).
@@ -1217,8 +1219,10 @@ static int tiled_ok(const mbs_scenario_s *s, int prec, int T) {
     if (!uses_tc(s, prec))
       return fail(MBS_E_INVALID,
                   "tiled kernels for N >= 4 need FP32, one medium and no per-cell factors; use the plain algorithm");
-    if (T < 1 || T > mbs::tiled_tc_max_steps())
-      return fail(MBS_E_INVALID, "tile_steps must be in [1, %d] for N >= 4", mbs::tiled_tc_max_steps());
+    if (!mbs::tiled_tc_geometry_ok(s->dev->nx, s->tc_cells, T))
+      return fail(MBS_E_INVALID,
+                  "tile_steps %d does not fit %d-cell tensor-core tiles on this grid (1..20 always fit 128-cell tiles)",
+                  T, s->tc_cells);
     return MBS_OK;
   }
   if (!mbs::tiled_supported(prec, s->N) || (s->has_pcell && s->N != 2))
@@ -1301,10 +1305,16 @@ static std::vector<int> tile_candidates(int N, long long nt) {
 
 static int tiled_launch(const mbs_scenario_s *s, const mbs::Args &a, long long n0, int ns, int T, int cur,
                         cudaStream_t st) {
-  return s->N >= 4 ? mbs::launch_tiled_tc(a, n0, ns, T, cur, st) : mbs::launch_tiled(a, n0, ns, T, cur, st);
+  return s->N >= 4 ? mbs::launch_tiled_tc(a, s->tc_cells, n0, ns, T, cur, st)
+                   : mbs::launch_tiled(a, n0, ns, T, cur, st);
 }
 
-// time `run(T)` (which enqueues one launch) for every candidate; -1 on error
+// Candidate codes: the tile depth, plus 1000 for 256-cell tensor-core tiles.
+static int code_steps(int code) { return code % 1000; }
+static int code_cells(int code) { return code >= 1000 ? 256 : 128; }
+
+// time `run(code, cur)` (which enqueues one launch) for every candidate; -1
+// on error
 template <class Run>
 static int tune_loop(const std::vector<int> &cands, cudaStream_t st, Run run) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1324,7 +1334,7 @@ static int tune_loop(const std::vector<int> &cands, cudaStream_t st, Run run) {
       best = -1;
       break;
     }
-    const float per_step = ms / (3.0f * T);
+    const float per_step = ms / (3.0f * code_steps(T));
     if (per_step < best_t) {
       best_t = per_step;
       best = T;
@@ -1335,6 +1345,7 @@ static int tune_loop(const std::vector<int> &cands, cudaStream_t st, Run run) {
   return best;
 }
 
+// returns the winning candidate code (see code_steps / code_cells)
 static int autotune_one(mbs_scenario_s *s, int prec, const mbs::Args &a, cudaStream_t st) {
   char key[128];
   std::snprintf(key, sizeof key, "1:%d:%d:%d:%d:%d", s->N, prec, s->N >= 4 ? 9 : mbs::tiled_variant(a), s->dev->nx,
@@ -1345,10 +1356,23 @@ static int autotune_one(mbs_scenario_s *s, int prec, const mbs::Args &a, cudaStr
     if (it != g_tune.end()) return it->second;
   }
   std::vector<int> cands;
-  for (int T : tile_candidates(s->N, s->nt))
-    if (s->N >= 4 ? T <= mbs::tiled_tc_max_steps() : T <= mbs::tile_max_steps(s->N)) cands.push_back(T);
+  for (int T : tile_candidates(s->N, s->nt)) {
+    if (s->N < 4) {
+      if (T <= mbs::tile_max_steps(s->N)) cands.push_back(T);
+      continue;
+    }
+    if (mbs::tiled_tc_geometry_ok(s->dev->nx, 128, T)) cands.push_back(T);
+  }
+  if (s->N >= 4)
+    for (int T : {12, 16, 20, 24, 32, 40})
+      if (T <= s->nt && mbs::tiled_tc_geometry_ok(s->dev->nx, 256, T)) cands.push_back(1000 + T);
   if (cands.size() < 2) return default_tile_steps(s->N);
-  const int T = tune_loop(cands, st, [&](int t, int cur) { return tiled_launch(s, a, 0, t, t, cur, st); });
+  const int saved = s->tc_cells;
+  const int T = tune_loop(cands, st, [&](int c, int cur) {
+    s->tc_cells = code_cells(c);
+    return tiled_launch(s, a, 0, code_steps(c), code_steps(c), cur, st);
+  });
+  s->tc_cells = saved;
   if (T < 0) return default_tile_steps(s->N);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = T;
@@ -1361,13 +1385,16 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
   if (rc) return rc;
   mbs::Args a = make_args(s, prec);
   int algo = o.algo == MBS_ALGO_AUTO ? default_algo(s, prec) : o.algo;
-  int T = o.tile_steps > 0 ? o.tile_steps : default_tile_steps(s->N);
+  s->tc_cells = (o.flags & MBS_SOLVE_WIDE_TILES) ? 256 : 128;
+  int T = o.tile_steps > 0 ? o.tile_steps : default_tile_steps(s->N, s->tc_cells);
   const int chk = o.check_every > 0 ? o.check_every : 0;
   int cur = 0;
   if (algo == MBS_ALGO_TILED) {
     if ((rc = tiled_ok(s, prec, T))) return rc;
     if (o.tile_steps <= 0 && (o.flags & MBS_SOLVE_AUTOTUNE)) {
-      T = autotune_one(s, prec, a, st);
+      const int code = autotune_one(s, prec, a, st);
+      T = code_steps(code);
+      if (s->N >= 4) s->tc_cells = code_cells(code);
       if ((rc = prepare_solve(s, prec, st))) return rc;   // the trials advanced the state
     }
     long long done = 0;

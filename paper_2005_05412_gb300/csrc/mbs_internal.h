@@ -121,10 +121,12 @@ int launch_check(const Args &a, int cur, const int *cells, int n_cells, double *
                  double *out_trace_dev, const void *zref_full, const void *V, void *stream);
 
 // Tensor-core tiled kernel for N = 4..6 (mbs_tc.cu): FP32 state, one medium
-// parameter slot, no per-cell operators, 1 <= T <= tiled_tc_max_steps().
+// parameter slot, no per-cell operators; tiles of `cells` = 128 or 256 cells
+// (one or two 128-row MMA groups per block); T must pass
+// tiled_tc_geometry_ok for the grid.
 int tiled_tc_supported(int prec, int N);
-int tiled_tc_max_steps();
-int launch_tiled_tc(const Args &a, long long n0, int nsteps, int T, int cur, void *stream);
+bool tiled_tc_geometry_ok(int n_cells, int cells, int T);
+int launch_tiled_tc(const Args &a, int cells, long long n0, int nsteps, int T, int cur, void *stream);
 // Host: the tensor-core tiles' constant table for N levels from the FP64
 // parameter block of the medium (layout of q_stride): the TF32 hi/lo weight
 // operands in their shared-memory layout, the reference coherences and the

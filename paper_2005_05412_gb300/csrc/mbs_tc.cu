@@ -35,7 +35,7 @@
 namespace mbs {
 namespace dev {
 
-template <int N>
+template <int N, int G>
 struct TcShape {
   static constexpr int K = N * N - 1;                 // deviation components
   static constexpr int P = N * (N - 1) / 2;           // coherence pairs
@@ -47,16 +47,18 @@ struct TcShape {
   static constexpr int KA = (K + 1 + 7) / 8 * 8;      // MMA K: [u, 1] padded to the TF32 K step (8)
   static constexpr int NO = (K + SH + 1 + 15) / 16 * 16;   // MMA N: [0^SH, (A - I) u + c, w . u + w0], padded to 16
   static constexpr int NCH = (K + SH + 15) / 16;      // 16-column chunks holding the K components
-  static constexpr int M = 128;                       // cells per tile = MMA M = threads per block
+  static constexpr int M = 128 * G;                   // cells per tile = threads per block: G MMA row groups of 128
   static constexpr int W = M / 32;                    // warps
   // TMEM columns: accumulator [0, NO) (component i at column i + SH, the
   // coupling at K + SH), Kahan compensation words [C_COL, C_COL + 16 NCH)
   // in the same per-chunk positions.  Each step the threads seed the
   // accumulator with the rotation increments (R - 1) x and the MMA adds the
   // propagator's increment onto them.
+  // per row group; group h uses columns [h GCOLS, (h + 1) GCOLS)
   static constexpr int C_COL = NO;
-  static constexpr int TCOLS = C_COL + 16 * NCH <= 32 ? 32 : C_COL + 16 * NCH <= 64 ? 64 : 128;   // power of 2
-  static_assert(C_COL + 16 * NCH <= TCOLS, "TMEM columns");
+  static constexpr int GCOLS = C_COL + 16 * NCH <= 32 ? 32 : C_COL + 16 * NCH <= 64 ? 64 : 128;
+  static constexpr int TCOLS = G * GCOLS;   // a power of 2 for G = 1, 2
+  static_assert(C_COL + 16 * NCH <= GCOLS && TCOLS <= 256, "TMEM columns");
   static constexpr int CH = KA / 4;                   // 16-byte chunks per operand row
   // canonical K-major layout without swizzle: 8-row x 16-byte core matrices,
   // K-adjacent core matrices LBO bytes apart, row-adjacent ones SBO apart
@@ -231,10 +233,10 @@ __device__ __forceinline__ void sts128(uint32_t addr, float a, float b, float c,
 // Per thread the deviation lives in registers and its Kahan compensation in
 // the thread's TMEM lane, which keeps the block at <= 128 registers per
 // thread: four blocks (16 warps) per SM.
-template <int N>
-__global__ void __launch_bounds__(128, 4)
+template <int N, int G>
+__global__ void __launch_bounds__(128 * G, 4 / G)
     k_tiled_tc(const __grid_constant__ Args a, long long n0, int nsteps, int T, int cur) {
-  using S = TcShape<N>;
+  using S = TcShape<N, G>;
   constexpr int K = S::K, P = S::P, NP = S::NP, SH = S::SH;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
@@ -324,7 +326,8 @@ __global__ void __launch_bounds__(128, 4)
   // field angles of the pairs (0, k), k = 1..N-1; every other pair's angle
   // is a difference of two of them (theta_jk = theta_0k - theta_0j)
   const float *kap0 = reinterpret_cast<const float *>(smem + S::OFF_KP);
-  const uint32_t t_row = tmem + ((uint32_t)(wib * 32) << 16);   // this warp's TMEM lanes
+  // this warp's TMEM lanes (warp w reaches lanes 32 (w mod 4) ..) in its row group's columns
+  const uint32_t t_row = tmem + ((uint32_t)((wib & 3) * 32) << 16) + (uint32_t)((wib >> 2) * S::GCOLS);
   const uint32_t t_cmp = t_row + S::C_COL;                        // its compensation words
   {
     // compensation words of the cell into TMEM (column i + SH)
@@ -341,7 +344,7 @@ __global__ void __launch_bounds__(128, 4)
     }
     tmem_wait_st();
   }
-  constexpr uint32_t IDESC = idesc_tf32(S::M, S::NO);
+  constexpr uint32_t IDESC = idesc_tf32(128, S::NO);
   uint32_t phase = 0;
   bool timed_out = false;   // this thread's wait gave up
   int stop = 0;             // some thread's wait gave up (block-uniform)
@@ -459,11 +462,16 @@ __global__ void __launch_bounds__(128, 4)
       const uint64_t dA_hi = umma_desc(sA_hi, S::LBO_A, S::SBO), dA_lo = umma_desc(sA_lo, S::LBO_A, S::SBO);
       const uint64_t dB_hi = umma_desc(sB_hi, S::LBO_B, S::SBO), dB_lo = umma_desc(sB_lo, S::LBO_B, S::SBO);
 #pragma unroll
-      for (int k = 0; k < S::KA / 8; ++k) {
-        const uint64_t oa = (uint64_t)((2 * k * S::LBO_A) >> 4), ob = (uint64_t)((2 * k * S::LBO_B) >> 4);
-        mma_tf32(tmem, dA_lo + oa, dB_hi + ob, IDESC, 1u);
-        mma_tf32(tmem, dA_hi + oa, dB_lo + ob, IDESC, 1u);
-        mma_tf32(tmem, dA_hi + oa, dB_hi + ob, IDESC, 1u);
+      for (int h = 0; h < G; ++h) {   // row group h: rows 128 h.., 16 row groups of 8 further in A
+        const uint32_t d = tmem + (uint32_t)(h * S::GCOLS);
+#pragma unroll
+        for (int k = 0; k < S::KA / 8; ++k) {
+          const uint64_t oa = (uint64_t)((2 * k * S::LBO_A + h * 16 * S::SBO) >> 4);
+          const uint64_t ob = (uint64_t)((2 * k * S::LBO_B) >> 4);
+          mma_tf32(d, dA_lo + oa, dB_hi + ob, IDESC, 1u);
+          mma_tf32(d, dA_hi + oa, dB_lo + ob, IDESC, 1u);
+          mma_tf32(d, dA_hi + oa, dB_hi + ob, IDESC, 1u);
+        }
       }
       mma_commit(bar);
     }
@@ -596,9 +604,9 @@ __global__ void __launch_bounds__(128, 4)
   }
 }
 
-template <int N>
+template <int N, int G>
 int tiled_tc_impl(const Args &a, long long n0, int nsteps, int T, int cur, cudaStream_t st) {
-  using S = TcShape<N>;
+  using S = TcShape<N, G>;
   static_assert(S::M - 5 <= PAD, "a tile reaches past the pad cells");
   static bool attr_set[64] = {};
   int dev = 0;
@@ -606,15 +614,15 @@ int tiled_tc_impl(const Args &a, long long n0, int nsteps, int T, int cur, cudaS
   if (e != cudaSuccess) return (int)e;
   if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
   if (!attr_set[dev]) {
-    e = cudaFuncSetAttribute(k_tiled_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
-    if (e == cudaSuccess)   // all of the unified L1/shared storage as shared memory: 3 tiles per SM
-      e = cudaFuncSetAttribute(k_tiled_tc<N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    e = cudaFuncSetAttribute(k_tiled_tc<N, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    if (e == cudaSuccess)   // all of the unified L1/shared storage as shared memory
+      e = cudaFuncSetAttribute(k_tiled_tc<N, G>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return (int)e;
     attr_set[dev] = true;
   }
   const int own = S::M - 2 * T;
   const int gs = (a.nx + own - 1) / own;
-  k_tiled_tc<N><<<gs, S::M, S::SMEM, st>>>(a, n0, nsteps, T, cur);
+  k_tiled_tc<N, G><<<gs, S::M, S::SMEM, st>>>(a, n0, nsteps, T, cur);
   return (int)cudaGetLastError();
 }
 
@@ -633,7 +641,7 @@ float tf32_host(float x) {
 
 template <int N>
 int tc_table_impl(const double *qb, float *out) {
-  using S = dev::TcShape<N>;
+  using S = dev::TcShape<N, 1>;
   if (!out) return S::TAB;
   constexpr int K = S::K, P = S::P;
   for (int i = 0; i < S::TAB; ++i) out[i] = 0.0f;
@@ -671,16 +679,38 @@ int tc_weight_table(int N, const double *qblk, float *out) {
 
 int tiled_tc_supported(int prec, int N) { return prec == 1 && N >= 4 && N <= 6; }
 
-int tiled_tc_max_steps() { return 20; }   // 32 - 12: room for the shift of the tile holding the last cell
+// The kernel's tile placement (as in k_tiled_tc): the tile that owns the
+// last cell starts 4 or 8 cells early when the last cell would be its first
+// owned cell or start a warp.  T is usable when, for this grid, the last cell
+// stays owned with its neighbour in the same warp and inside the light cone,
+// and cell 0's neighbour is in the same warp and inside the light cone.
+bool tiled_tc_geometry_ok(int nx, int cells, int T) {
+  if ((cells != 128 && cells != 256) || T < 1 || cells - 2 * T < 32 || nx < 1) return false;
+  const int own = cells - 2 * T;
+  auto start = [&](int c_own) {
+    int tb = c_own - T;
+    if (nx - 1 < c_own + own) {
+      if (nx - 1 == c_own || (nx - 1 - tb) % 32 == 0) tb -= 4;
+      if ((nx - 1 - tb) % 32 == 0) tb -= 4;
+    }
+    return tb;
+  };
+  const int c_last = (nx - 1) / own * own;
+  const int p = nx - 1 - start(c_last);          // tile position of the last cell
+  if (!(p >= T + 1 && p < cells - T && p % 32 != 0)) return false;
+  const int q = -start(0);                       // tile position of cell 0
+  return q % 32 != 31 && q + 1 <= cells - 1 - T;
+}
 
-int launch_tiled_tc(const Args &a, long long n0, int nsteps, int T, int cur, void *stream) {
+int launch_tiled_tc(const Args &a, int cells, long long n0, int nsteps, int T, int cur, void *stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (a.prec != 1 || a.n_slot != 1 || a.pcell || !a.tcw || a.n_probe > MAXPROBE || T < 1 || T > tiled_tc_max_steps())
+  if (a.prec != 1 || a.n_slot != 1 || a.pcell || !a.tcw || a.n_probe > MAXPROBE || !tiled_tc_geometry_ok(a.nx, cells, T))
     return (int)cudaErrorInvalidValue;
+  const bool wide = cells == 256;
   switch (a.N) {
-    case 4: return dev::tiled_tc_impl<4>(a, n0, nsteps, T, cur, st);
-    case 5: return dev::tiled_tc_impl<5>(a, n0, nsteps, T, cur, st);
-    case 6: return dev::tiled_tc_impl<6>(a, n0, nsteps, T, cur, st);
+    case 4: return wide ? dev::tiled_tc_impl<4, 2>(a, n0, nsteps, T, cur, st) : dev::tiled_tc_impl<4, 1>(a, n0, nsteps, T, cur, st);
+    case 5: return wide ? dev::tiled_tc_impl<5, 2>(a, n0, nsteps, T, cur, st) : dev::tiled_tc_impl<5, 1>(a, n0, nsteps, T, cur, st);
+    case 6: return wide ? dev::tiled_tc_impl<6, 2>(a, n0, nsteps, T, cur, st) : dev::tiled_tc_impl<6, 1>(a, n0, nsteps, T, cur, st);
   }
   return (int)cudaErrorInvalidValue;
 }

@@ -157,7 +157,7 @@ def test_tc_limits():
     p = ladder(6, 300, 40)
     dev = mbs.device_from_problem(p)
     sc = mbs.scenario_from_problem(dev, p)
-    for bad in (21, 40):
+    for bad in (50, 64):   # a 128-cell tile would own fewer than 32 cells
         with pytest.raises(mbs.MBSError) as e:
             mbs.mbs_solve([sc], "fp32", "tiled", tile_steps=bad)
         assert e.value.status == mbs.MBS_E_INVALID
@@ -165,3 +165,37 @@ def test_tc_limits():
         mbs.mbs_solve([sc], "fp64", "tiled")
     assert e.value.status == mbs.MBS_E_INVALID
     mbs.mbs_solve([sc], "fp64")                  # auto: the plain FP64 path
+
+
+@pytest.mark.parametrize("tile", [12, 20, 26, 40])
+def test_wide_tiles_vs_oracle(tile):
+    """256-cell tensor-core tiles (two 128-row MMA groups per block)."""
+    p = ladder(6, 1_777, 1_200)
+    ref = oracle_run("ladder6_1777", p)
+    got = mbs.run(p, precision="fp32", algo="tiled", tile_steps=tile, wide_tiles=True)
+    err = trace_errors(p, got["records"], ref["records"])
+    assert err.max() <= TOL32, err
+
+
+@pytest.mark.parametrize("tile", [8, 20, 24])
+def test_wide_tiles_right_boundary_at_tile_edge(tile):
+    own = 256 - 2 * tile
+    nx = 9 * own + 1
+    p = ladder(6, nx, 1_000)
+    p.probes = p.probes + [W.Probe(nx - 1, W.Q_E), W.Probe(nx - 2, W.Q_E), W.Probe(nx - 1, W.Q_H)]
+    a = mbs.run(p, precision="fp64", algo="plain")["records"]
+    b = mbs.run(p, precision="fp32", algo="tiled", tile_steps=tile, wide_tiles=True)["records"]
+    err = trace_errors(p, b, a)
+    assert err.max() <= TOL32, err
+
+
+def test_wide_tiles_reject_depths_outside_the_light_cone():
+    """T = 28 on 197 cells would leave the last cell outside its tile's owned
+    range after the shift that keeps it off a warp start: rejected."""
+    p = ladder(6, 197, 40)
+    dev = mbs.device_from_problem(p)
+    sc = mbs.scenario_from_problem(dev, p)
+    with pytest.raises(mbs.MBSError) as e:
+        mbs.mbs_solve([sc], "fp32", "tiled", tile_steps=28, wide_tiles=True)
+    assert e.value.status == mbs.MBS_E_INVALID
+    mbs.mbs_solve([sc], "fp32", "tiled", tile_steps=26, wide_tiles=True)
