@@ -250,6 +250,7 @@ def run_ours(args, rank, world, local):
         out["fp64_plain"] = fp64_plain(p, mbs, stream, torch)
         out["six_level"] = level_leg(mbs, stream, torch, "ladder_6lvl", 0, pk, clocks)
         out["three_level"] = level_leg(mbs, stream, torch, "lambda_3lvl", 0, pk, clocks)
+        out["cells"] = cells_leg(mbs, stream, torch, clocks)
         if not args.no_batch:
             out["batch"] = batch_leg(mbs, stream, torch, "fp32")
         out["e2e"] = e2e(p, mbs, args, torch, stream)
@@ -338,6 +339,52 @@ def level_leg(mbs, stream, torch, name, T, pk, clocks, reps=2, fp64_steps=1000):
     out["plain_sample"] = f"first {fp64_steps} steps"
     out["speedup_vs_fp64_plain"] = round(value / out["fp64_plain"], 1)
     return out
+
+
+def cells_leg(mbs, stream, torch, clocks, n_sys=131_072, n_steps=10_000, every=100, reps=2):
+    """Driven single cells (Nx = 1, the master equation alone): the V-type
+    three-level example as a batch of 131,072 systems (parameters +-10 %,
+    drive amplitude swept over 0.25..2 e0) x 10,000 steps over 80 fs, one
+    thread per system, populations recorded every 100 steps; FP32 and FP64;
+    the oracle's driven-cell solver timed on 32 of the systems."""
+    b = W.song_vtype(n_sys=n_sys, n_steps=n_steps, record_every=every)
+    c = mbs.cells_from_batch(b)
+    out = {}
+    for prec in ("fp32", "fp64"):
+        mbs.mbs_cells_solve(c, prec, stream=stream.cuda_stream)    # warm-up (allocates)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mbs.mbs_cells_solve(c, prec, stream=stream.cuda_stream)
+            e.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(e) / 1e3
+            best = t if best is None else min(best, t)
+        out[prec] = n_sys * n_steps / best / 1e9
+    K = 8
+    flops = 2 * K * K + 6 * 3 + 4 * K           # propagator apply, rotations, compensated adds
+    mhz = clocks.get("sm_mhz") or 2070.0
+    peak = 2 * 128 * 152 * mhz / 1e6             # FP32 FMA lanes x 2 flops x SMs x clock [TFLOP/s]
+    ach = flops * out["fp32"] * 1e9 / 1e12
+    res = {"value": round(out["fp32"], 2), "unit": METRIC, "fp64": round(out["fp64"], 2),
+           "workload": f"song_vtype: {n_sys} driven three-level systems x {n_steps} steps (Nx = 1)",
+           "roofline": {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                        "frac": round(ach / peak, 4), "alg_flops_per_cell_step": flops,
+                        "peak_source": "FP32 FMA rate of 152 SMs x 128 lanes at the sampled SM clock"}}
+    try:
+        import oracle
+        import time as _t
+        t0 = _t.perf_counter()
+        m = 32
+        for s in range(m):
+            oracle.cell_evolve(b.qms[s], b.dt, W.cell_field(b.drives[s], b.dt, n_steps))
+        res["cpu_oracle"] = {"value": round(m * n_steps / (_t.perf_counter() - t0) / 1e9, 5), "cores": 1,
+                             "sample": f"{m} systems x {n_steps} steps, one at a time on one core"}
+    except Exception as ex:   # the oracle is optional here
+        res["cpu_oracle"] = {"unavailable": str(ex)[:80]}
+    return res
 
 
 def batch_leg(mbs, stream, torch, precision):

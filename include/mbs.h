@@ -274,6 +274,47 @@ int mbs_scenario_counters(mbs_scenario_t s, long long *h2d_bytes, long long *d2h
  * streams, or from several host threads) race on it. */
 int mbs_check_rho_static(const double *rho, int n, int n_levels, double *out, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Driven single cells (Sec. 2.1, the borderline case Nx = 1: the master
+ * equation alone, "a solver for the Lindblad equation"; the V-type
+ * three-level application example of Sec. 4 is one such system).  A batch of
+ * n_sys independent systems, each with its own quantum description and its
+ * own prescribed field
+ *   E^n = e0 sech((t_n - t0)/tau) sin(omega t_n + phase),  t_n = n dt,
+ *   E^0 = 0 (the initial field),
+ * advances n_steps steps of the Strang splitting of Sec. 2.2 (step n uses
+ * E^n, as a grid cell under a hard source does).  One GPU thread per system.
+ * The populations rho_kk^{n+1/2} are recorded every record_every steps:
+ * record r holds step n = (r + 1) record_every - 1.  The density n3D and the
+ * source kind are not used (no field is fed back). */
+typedef struct mbs_cells_s *mbs_cells_t;
+
+/* Build the batch on the host (FP64 step operators per system; systems with
+ * the same tau, t0, omega, phase share one tabulated drive shape).  All
+ * systems must have the same level count, 2 or 3.  Inputs are copied.
+ * Returns MBS_OK, MBS_W_NOT_PSD (some system's dephasing rates) or an error
+ * (MBS_E_INVALID with the offending system in mbs_last_error). */
+int mbs_cells_create(const mbs_qm_desc *qms, int n_sys, double dt, long long n_steps,
+                     const mbs_source *drives, int record_every, mbs_cells_t *out);
+
+/* Run all systems from their initial states (FP32 with compensated sums, or
+ * FP64) on `cuda_stream` (cudaStream_t or NULL); device memory is allocated
+ * on the current device on the first solve of each precision.  Returns
+ * after completion; MBS_E_NUMERIC if a final density matrix is not finite or
+ * has an eigenvalue below -1e-6. */
+int mbs_cells_solve(mbs_cells_t c, int precision, void *cuda_stream);
+
+/* Copy system `sys`'s records, n_rec x N doubles (out[r N + k] =
+ * rho_kk of record r), n_rec = n_steps / record_every.  out == NULL: only
+ * *n_written (the count) is set. */
+int mbs_cells_fetch(mbs_cells_t c, int sys, double *out, size_t cap, size_t *n_written);
+
+/* Over all systems after the last solve: max |tr rho - 1|, smallest
+ * eigenvalue of rho. */
+int mbs_cells_stats(mbs_cells_t c, double *max_trace_dev, double *min_eig);
+
+void mbs_cells_destroy(mbs_cells_t c);
+
 void mbs_scenario_destroy(mbs_scenario_t s);
 void mbs_device_destroy(mbs_device_t d);
 

@@ -79,7 +79,8 @@ _lib = None
 # every symbol include/mbs.h declares
 EXPORTS = ["mbs_device_create", "mbs_device_destroy", "mbs_device_propagators", "mbs_scenario",
            "mbs_scenario_destroy", "mbs_scenario_info", "mbs_scenario_stats", "mbs_scenario_counters", "mbs_solve",
-           "mbs_fetch_records", "mbs_last_error", "mbs_abi_version", "mbs_check_rho_static", "mbs_scenario_tile"]
+           "mbs_fetch_records", "mbs_last_error", "mbs_abi_version", "mbs_check_rho_static", "mbs_scenario_tile",
+           "mbs_cells_create", "mbs_cells_solve", "mbs_cells_fetch", "mbs_cells_stats", "mbs_cells_destroy"]
 
 
 def lib():
@@ -102,6 +103,12 @@ def lib():
         L.mbs_scenario_stats.argtypes = [vp, C.POINTER(d), C.POINTER(d), C.POINTER(ll)]
         L.mbs_scenario_counters.argtypes = [vp, C.POINTER(ll), C.POINTER(ll), C.POINTER(ll)]
         L.mbs_scenario_tile.argtypes = [vp, C.POINTER(i)]
+        L.mbs_cells_create.argtypes = [C.POINTER(_QmDesc), i, d, ll, C.POINTER(_Source), i, C.POINTER(vp)]
+        L.mbs_cells_solve.argtypes = [vp, i, vp]
+        L.mbs_cells_fetch.argtypes = [vp, i, vp, C.c_size_t, C.POINTER(C.c_size_t)]
+        L.mbs_cells_stats.argtypes = [vp, C.POINTER(d), C.POINTER(d)]
+        L.mbs_cells_destroy.argtypes = [vp]
+        L.mbs_cells_destroy.restype = None
         L.mbs_solve.argtypes = [C.POINTER(vp), i, C.POINTER(_Opts), vp]
         L.mbs_fetch_records.argtypes = [vp, i, vp, C.c_size_t, C.POINTER(C.c_size_t)]
         L.mbs_last_error.restype = C.c_char_p
@@ -172,23 +179,26 @@ class Scenario:
             pass
 
 
+def _qm_desc(q, keep):
+    """Marshal one quantum description (buffers appended to `keep`)."""
+    n = q.n_levels
+    h0, mu, rho = _cbuf(q.h0, n * n), _cbuf(q.mu, n * n), _cbuf(q.rho_init, n * n)
+    rates = np.ascontiguousarray(np.asarray(q.lindblad_rates, np.float64).reshape(-1))
+    nl = rates.size
+    ops = _cbuf(q.lindblad_ops, nl * n * n) if nl else None
+    scat = None if q.scattering is None else np.ascontiguousarray(np.asarray(q.scattering, np.float64).reshape(-1))
+    deph = None if q.pure_dephasing is None else np.ascontiguousarray(np.asarray(q.pure_dephasing, np.float64).reshape(-1))
+    keep += [h0, mu, rho, rates, ops, scat, deph]
+    return _QmDesc(n, float(q.density), _p(h0), _p(mu), nl, _p(rates) if nl else None, _p(ops),
+                   _p(scat), _p(deph), _p(rho))
+
+
 def mbs_device_create(qms, materials, regions, length, n_cells, bc=(0.0, 0.0), jitter=None) -> Device:
     """qms: objects with n_levels, density, h0, mu, rho_init, lindblad_rates,
     lindblad_ops, scattering, pure_dephasing; materials: eps_r, mu_r, sigma,
     overlap, qm; regions: material, x_start, x_end."""
     keep = []
-    descs = []
-    for q in qms:
-        n = q.n_levels
-        h0, mu, rho = _cbuf(q.h0, n * n), _cbuf(q.mu, n * n), _cbuf(q.rho_init, n * n)
-        rates = np.ascontiguousarray(np.asarray(q.lindblad_rates, np.float64).reshape(-1))
-        nl = rates.size
-        ops = _cbuf(q.lindblad_ops, nl * n * n) if nl else None
-        scat = None if q.scattering is None else np.ascontiguousarray(np.asarray(q.scattering, np.float64).reshape(-1))
-        deph = None if q.pure_dephasing is None else np.ascontiguousarray(np.asarray(q.pure_dephasing, np.float64).reshape(-1))
-        keep += [h0, mu, rho, rates, ops, scat, deph]
-        descs.append(_QmDesc(n, float(q.density), _p(h0), _p(mu), nl, _p(rates) if nl else None, _p(ops),
-                             _p(scat), _p(deph), _p(rho)))
+    descs = [_qm_desc(q, keep) for q in qms]
     qarr = (_QmDesc * max(1, len(descs)))(*descs)
     marr = (_Material * len(materials))(*[_Material(m.eps_r, m.mu_r, m.sigma, m.overlap, m.qm) for m in materials])
     rarr = (_Region * len(regions))(*[_Region(r.material, r.x_start, r.x_end) for r in regions])
@@ -288,6 +298,63 @@ def mbs_check_rho_static(rho_ptr: int, n: int, n_levels: int, out_ptr: int, stre
 
 def mbs_abi_version() -> int:
     return int(lib().mbs_abi_version())
+
+
+class Cells:
+    """Owns an mbs_cells_t (a batch of driven single cells)."""
+
+    def __init__(self, handle, status, n_sys, n_levels, keep):
+        self.handle = handle
+        self.status = status
+        self.n_sys = n_sys
+        self.n_levels = n_levels
+        self._keep = keep
+
+    def close(self):
+        if self.handle:
+            lib().mbs_cells_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mbs_cells_create(qms, dt, n_steps, drives, record_every=1) -> Cells:
+    keep = []
+    qarr = (_QmDesc * len(qms))(*[_qm_desc(q, keep) for q in qms])
+    darr = (_Source * len(drives))(*[_Source(s.kind, s.cell, s.e0, s.tau, s.t0, s.omega, s.phase) for s in drives])
+    h = C.c_void_p()
+    rc = _check(lib().mbs_cells_create(qarr, len(qms), float(dt), int(n_steps), darr, int(record_every),
+                                       C.byref(h)))
+    return Cells(h.value, rc, len(qms), qms[0].n_levels, keep)
+
+
+def mbs_cells_solve(cells: Cells, precision="fp32", stream=None) -> int:
+    return _check(lib().mbs_cells_solve(cells.handle, PREC[precision] if isinstance(precision, str) else int(precision),
+                                        None if stream is None else C.c_void_p(int(stream))))
+
+
+def mbs_cells_fetch(cells: Cells, sys: int) -> np.ndarray:
+    """Populations of system `sys`: array (n_rec, N), row r = record r."""
+    n = C.c_size_t()
+    _check(lib().mbs_cells_fetch(cells.handle, int(sys), None, 0, C.byref(n)))
+    out = np.empty(n.value, np.float64)
+    _check(lib().mbs_cells_fetch(cells.handle, int(sys), out.ctypes.data, out.size, C.byref(n)))
+    return out.reshape(-1, cells.n_levels)
+
+
+def mbs_cells_stats(cells: Cells):
+    tr, mn = C.c_double(), C.c_double()
+    _check(lib().mbs_cells_stats(cells.handle, C.byref(tr), C.byref(mn)))
+    return dict(max_trace_dev=tr.value, min_eig=mn.value)
+
+
+def cells_from_batch(b) -> Cells:
+    """Marshal a workloads.CellBatch-like description."""
+    return mbs_cells_create(b.qms, b.dt, b.n_steps, b.drives, b.record_every)
 
 
 # ------------------------------------------------------------ conveniences

@@ -105,6 +105,24 @@ struct Args {
   int *flags;                  // [4] device status words
 };
 
+// Batched single-cell solver (mbs_cells.cu): one thread per driven system.
+struct CellsArgs {
+  int prec, N, n_sys;
+  long long nt;
+  int every;               // record every `every` steps
+  const void *prm;         // [rows][n_sys]: A - I | c | kap | zr | population functionals
+  void *D, *C;             // [K][n_sys] deviation / Kahan compensation (updated in place)
+  const void *amp;         // [n_sys] drive amplitude
+  const int *tab_id;       // [n_sys] drive shape
+  const void *tab;         // drive shapes: FP64 [n_tab][nt]; FP32 [n_tab][2][nt] (high, low words)
+  long long tab_stride;    // reals per shape
+  void *rec;               // [n_rec][N][n_sys] populations
+  const double *zref;      // [n_sys][N*N] reference states (full real coordinates)
+  int *flags;              // [4]
+};
+int launch_cells(const CellsArgs &a, long long n0, int nsteps, void *stream);
+int launch_cells_check(const CellsArgs &a, double *min_eig, double *tr_dev, void *stream);
+
 // Records `msg` as the calling thread's last error (mbs_last_error) and
 // returns `code` (mbs_host.cpp).
 int set_error(int code, const char *msg);

@@ -480,3 +480,34 @@ def test_courant_one_is_unstable_in_a_dense_medium():
     grow_1, grow_s = (b / a for a, b in out.values())
     assert grow_1 > 100.0
     assert grow_s < 10.0
+
+
+def test_vtype_relaxation_closed_form():
+    """The V-type example's relaxation (equal scattering rates g between all
+    three levels, Eq. relax_pop) with no field: from |1><1| the populations
+    obey p1' = g (p2 + p3) - 2 g p1, so p1(t) = 1/3 + 2/3 exp(-3 g t) and
+    p2 = p3 = (1 - p1)/2; the state after step n is at t = (n + 1) dt."""
+    import workloads as W
+    qm = W.song_vtype_qm()
+    g, dt, nt = 1e10, 8e-14, 400        # long steps: the decay is visible
+    traj = oracle.cell_evolve(qm, dt, np.zeros(nt))
+    t = (np.arange(nt) + 1) * dt
+    p1 = 1.0 / 3.0 + 2.0 / 3.0 * np.exp(-3.0 * g * t)
+    np.testing.assert_allclose(traj[:, 0, 0].real, p1, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(traj[:, 1, 1].real, (1 - p1) / 2, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(traj[:, 2, 2].real, (1 - p1) / 2, rtol=0, atol=1e-12)
+
+
+def test_vtype_weak_drive_stays_near_ground():
+    """A drive far below the example's amplitude (1e-4 e0) moves almost no
+    population: first-order perturbation theory bounds the excited
+    populations by (mu E0 tau / hbar)^2 ~ 1e-8 (plus relaxation ~ 2e-3 at
+    80 fs, which the closed form above gives)."""
+    import workloads as W
+    qm = W.song_vtype_qm()
+    d = W.song_vtype_drive(e0=3.5471e9 * 1e-4)
+    dt, nt = 8e-18, 10_000
+    traj = oracle.cell_evolve(qm, dt, W.cell_field(d, dt, nt))
+    t = (np.arange(nt) + 1) * dt
+    p1 = 1.0 / 3.0 + 2.0 / 3.0 * np.exp(-3.0 * 1e10 * t)
+    assert np.max(np.abs(traj[:, 0, 0].real - p1)) < 1e-6

@@ -381,6 +381,76 @@ def batch_mixed(n_sims=512, seed=4, min_cells=1024, max_cells=65536,
     return out
 
 
+@dataclass
+class CellBatch:
+    """Independent driven quantum systems without propagation (the borderline
+    case Nx = 1 of Sec. 2.1): system s evolves under the field
+    drives[s].waveform(n dt) at step n (0 at n = 0)."""
+    name: str
+    qms: List[QM]
+    drives: List[Source]
+    dt: float
+    n_steps: int
+    record_every: int = 1
+
+
+def song_vtype_qm(scale_e=1.0, scale_d=1.0, scale_g=1.0) -> QM:
+    """The driven V-type three-level system of the paper's application example
+    (atomic rubidium after Song et al.): level energies 0, 2.3717e15 hbar,
+    2.4165e15 hbar; dipole elements mu_12 = -e 9.2374e-11 m, mu_13 = sqrt(2)
+    mu_12, mu_23 = 0; scattering rate 1e10 s^-1 between every pair of levels,
+    no pure dephasing; rho(0) = |1><1|; n3D = 6e24 m^-3.  The scale factors
+    multiply the energies, the dipole elements and the rates."""
+    n = 3
+    en = np.array([0.0, 2.3717e15, 2.4165e15]) * HBAR * scale_e
+    d = -E_CHARGE * 9.2374e-11 * scale_d
+    mu = np.zeros((n, n), complex)
+    mu[0, 1] = mu[1, 0] = d
+    mu[0, 2] = mu[2, 0] = d * math.sqrt(2.0)
+    scat = np.full((n, n), 1e10 * scale_g)
+    np.fill_diagonal(scat, 0.0)
+    return QM(n, 6e24, np.diag(en).astype(complex), mu, _ketbra(n, 0, 0), scattering=scat,
+              pure_dephasing=np.zeros(3))
+
+
+def song_vtype_drive(e0=3.5471e9) -> Source:
+    """The sech drive of the V-type example, in the reading (amplitude,
+    frequency [Hz], t0 in units of tau, 1/tau, phase) of the listing's
+    numbers: e0 = 3.5471e9 V/m, omega = 2 pi 3.8118e14 rad/s, tau = 5 fs/1.76,
+    t0 = 17.248 tau, phase -pi/2."""
+    tau = 5e-15 / 1.76
+    return Source(SRC_HARD, 0, e0, tau, 17.248 * tau, 2.0 * math.pi * 3.8118e14, -math.pi / 2.0)
+
+
+def song_vtype(n_sys=1, seed=5, spread=0.1, n_steps=10_000, t_end=80e-15, record_every=1,
+               amp_range=(0.25, 2.0)) -> CellBatch:
+    """The V-type example as a batch: system 0 is the paper's system under its
+    drive; systems s > 0 have energies, dipoles and rates scaled by
+    (1 + spread U(-1, 1)) each and the drive amplitude swept uniformly over
+    amp_range x e0 (seeded).  Nt steps over t_end: dt = t_end / Nt."""
+    u = uniform01(seed, 4 * n_sys).reshape(n_sys, 4)
+    qms, drives = [], []
+    base = song_vtype_drive()
+    for s in range(n_sys):
+        if s == 0:
+            qms.append(song_vtype_qm())
+            drives.append(base)
+            continue
+        f = [1.0 + spread * (2.0 * u[s, k] - 1.0) for k in range(3)]
+        qms.append(song_vtype_qm(*f))
+        a = amp_range[0] + (amp_range[1] - amp_range[0]) * u[s, 3]
+        drives.append(Source(SRC_HARD, 0, base.e0 * a, base.tau, base.t0, base.omega, base.phase))
+    return CellBatch("song_vtype", qms, drives, t_end / n_steps, n_steps, record_every)
+
+
+def cell_field(drive: Source, dt: float, n_steps: int) -> np.ndarray:
+    """The prescribed field sequence E^n of a driven cell: the waveform at
+    t_n = n dt for n >= 1, and the initial field 0 at n = 0."""
+    e = np.asarray(drive.waveform(np.arange(n_steps) * dt), np.float64)
+    e[0] = 0.0
+    return e
+
+
 WORKLOADS = {
     "sit_2lvl": sit_2lvl,
     "sit_2lvl_jitter": sit_2lvl_jitter,
