@@ -251,6 +251,7 @@ def run_ours(args, rank, world, local):
         out["six_level"] = level_leg(mbs, stream, torch, "ladder_6lvl", 0, pk, clocks)
         out["three_level"] = level_leg(mbs, stream, torch, "lambda_3lvl", 0, pk, clocks)
         out["cells"] = cells_leg(mbs, stream, torch, clocks)
+        out["n_scaling"] = n_scaling_leg(mbs, stream, torch)
         if not args.no_batch:
             out["batch"] = batch_leg(mbs, stream, torch, "fp32")
         out["e2e"] = e2e(p, mbs, args, torch, stream)
@@ -339,6 +340,41 @@ def level_leg(mbs, stream, torch, name, T, pk, clocks, reps=2, fp64_steps=1000):
     out["plain_sample"] = f"first {fp64_steps} steps"
     out["speedup_vs_fp64_plain"] = round(value / out["fp64_plain"], 1)
     return out
+
+
+def n_scaling_leg(mbs, stream, torch, n_cells=524_288, n_steps=10_000, fp64_steps=500):
+    """Throughput against the number of levels: the anharmonic ladder of the
+    paper's six-level example (Gaussian source) for N = 2..6 on 524,288 cells
+    x 10,000 steps; FP32 with autotuned tiles (CUDA-core tiles for N = 2, 3,
+    tensor-core tiles for N >= 4) and the FP64 plain path on its first 500
+    steps."""
+    out = {}
+    for n in range(2, 7):
+        p = W.ladder_anharmonic(n, n_cells=n_cells, n_steps=n_steps)
+        dev = mbs.device_from_problem(p)
+        sc = mbs.scenario_from_problem(dev, p)
+        mbs.mbs_solve([sc], "fp32", "tiled", stream=stream.cuda_stream, autotune=True)   # tunes
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mbs.mbs_solve([sc], "fp32", "tiled", stream=stream.cuda_stream, autotune=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        v32 = n_cells * n_steps / (a.elapsed_time(b) / 1e3) / 1e9
+        q = p.replace(n_steps=fp64_steps)
+        dq = mbs.device_from_problem(q)
+        sq = mbs.scenario_from_problem(dq, q)
+        mbs.mbs_solve([sq], "fp64", "plain", stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        mbs.mbs_solve([sq], "fp64", "plain", stream=stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        v64 = n_cells * fp64_steps / (a.elapsed_time(b) / 1e3) / 1e9
+        out[f"N={n}"] = {"fp32": round(v32, 2), "fp64_plain": round(v64, 3), "tile_steps": mbs.mbs_scenario_tile(sc),
+                         "kernel": "tensor-core tiles" if n >= 4 else "CUDA-core tiles"}
+    return {"unit": METRIC, "workload": f"ladder_anharmonic: {n_cells} cells x {n_steps} steps, N = 2..6, "
+                                        "Gaussian source", "by_levels": out}
 
 
 def cells_leg(mbs, stream, torch, clocks, n_sys=131_072, n_steps=10_000, every=100, reps=2):

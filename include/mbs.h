@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define MBS_ABI_VERSION 1
+#define MBS_ABI_VERSION 2
 
 typedef enum {
     MBS_OK = 0,
@@ -119,13 +119,18 @@ enum { MBS_SRC_TFSF_RIGHT = 0, /* one-way injection of a +x travelling wave:
                                   (needs cell <= n_cells - 3) */
        MBS_SRC_HARD = 2 };     /* E^{n+1} at `cell` is set to the waveform */
 
-/* Source (Sec. 3.1.2, classes source / sech_pulse): waveform
- * S(t) = e0 sech((t - t0)/tau) sin(omega t + phase) [V/m].  Soft sources
- * are total-field/scattered-field injections that add the incident wave
- * and stay transparent to returning waves. */
+enum { MBS_SHAPE_SECH = 0,     /* envelope sech((t - t0)/tau) (class sech_pulse) */
+       MBS_SHAPE_GAUSS = 1 };   /* envelope exp(-((t - t0)/tau)^2) (class gaussian_pulse) */
+
+/* Source (Sec. 3.1.2, classes source / sech_pulse / gaussian_pulse):
+ * waveform S(t) = e0 envelope(t) sin(omega t + phase) [V/m] with the
+ * envelope chosen by `shape`.  Soft sources are total-field/scattered-field
+ * injections that add the incident wave and stay transparent to returning
+ * waves. */
 typedef struct {
     int kind; int cell;
     double e0, tau, t0, omega, phase;
+    int shape;                  /* MBS_SHAPE_* */
 } mbs_source;
 
 enum { MBS_Q_E = 0,       /* E at the cell centre, E^{n+1} [V/m] */
@@ -280,7 +285,8 @@ int mbs_check_rho_static(const double *rho, int n, int n_levels, double *out, vo
  * three-level application example of Sec. 4 is one such system).  A batch of
  * n_sys independent systems, each with its own quantum description and its
  * own prescribed field
- *   E^n = e0 sech((t_n - t0)/tau) sin(omega t_n + phase),  t_n = n dt,
+ *   E^n = e0 envelope(t_n) sin(omega t_n + phase),  t_n = n dt
+ *   (the source's shape: sech((t - t0)/tau) or exp(-((t - t0)/tau)^2)),
  *   E^0 = 0 (the initial field),
  * advances n_steps steps of the Strang splitting of Sec. 2.2 (step n uses
  * E^n, as a grid cell under a hard source does).  One GPU thread per system.

@@ -60,7 +60,7 @@ class _Reg(C.Structure):
 
 class _Src(C.Structure):
     _fields_ = [("kind", C.c_int), ("cell", C.c_int), ("e0", C.c_double), ("tau", C.c_double),
-                ("t0", C.c_double), ("omega", C.c_double), ("phase", C.c_double)]
+                ("t0", C.c_double), ("omega", C.c_double), ("phase", C.c_double), ("shape", C.c_int)]
 
 
 class _Probe(C.Structure):
@@ -184,8 +184,8 @@ def run(problem, n_threads: int = 0, check_invariants: bool = False):
     mats = (_Mat * len(problem.materials))(*[_Mat(m.eps_r, m.mu_r, m.sigma, m.overlap, m.qm)
                                                for m in problem.materials])
     regs = (_Reg * len(problem.regions))(*[_Reg(r.material, r.x_start, r.x_end) for r in problem.regions])
-    srcs = (_Src * max(1, len(problem.sources)))(*[_Src(s.kind, s.cell, s.e0, s.tau, s.t0, s.omega, s.phase)
-                                                   for s in problem.sources])
+    srcs = (_Src * max(1, len(problem.sources)))(*[_Src(s.kind, s.cell, s.e0, s.tau, s.t0, s.omega, s.phase,
+                                                        getattr(s, "shape", 0)) for s in problem.sources])
     prbs = (_Probe * max(1, len(problem.probes)))(*[_Probe(p.cell, p.quantity, p.i, p.j)
                                                      for p in problem.probes])
     jit = None

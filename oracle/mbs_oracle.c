@@ -71,7 +71,7 @@ typedef struct {
 
 typedef struct { double eps_r, mu_r, sigma, overlap; int qm; } orc_mat;
 typedef struct { int mat; double x0, x1; } orc_region;
-typedef struct { int kind; int cell; double e0, tau, t0, omega, phase; } orc_source;
+typedef struct { int kind; int cell; double e0, tau, t0, omega, phase; int shape; } orc_source;
 typedef struct { int cell; int q; int i, j; } orc_probe;
 
 typedef struct {
@@ -404,9 +404,14 @@ int orc_cell_evolve(const orc_qm *qm, double dt, long nt, const double *e, doubl
 }
 
 /* ---------------------------------------------------------- full sweep */
+/* Sec. 3.1.2, classes sech_pulse (shape 0) and gaussian_pulse (shape 1):
+ * e0 envelope((t - t0)/tau) sin(omega t + phase), the Gaussian envelope
+ * read as exp(-x^2) (the paper names the class only) */
 static double waveform(const orc_source *s, double t)
 {
-    return s->e0 / cosh((t - s->t0) / s->tau) * sin(s->omega * t + s->phase);
+    const double x = (t - s->t0) / s->tau;
+    const double env = s->shape == 1 ? exp(-x * x) : 1.0 / cosh(x);
+    return s->e0 * env * sin(s->omega * t + s->phase);
 }
 
 /* smallest eigenvalue of a Hermitian N x N matrix (N <= 8) via orc_eigh */

@@ -59,7 +59,7 @@ class _BC(C.Structure):
 
 class _Source(C.Structure):
     _fields_ = [("kind", C.c_int), ("cell", C.c_int), ("e0", C.c_double), ("tau", C.c_double),
-                ("t0", C.c_double), ("omega", C.c_double), ("phase", C.c_double)]
+                ("t0", C.c_double), ("omega", C.c_double), ("phase", C.c_double), ("shape", C.c_int)]
 
 
 class _Probe(C.Structure):
@@ -72,6 +72,7 @@ class _Opts(C.Structure):
 
 
 MBS_SOLVE_ONE_AT_A_TIME, MBS_SOLVE_AUTOTUNE, MBS_SOLVE_GRAPH, MBS_SOLVE_WIDE_TILES = 1, 2, 4, 8
+MBS_SHAPE_SECH, MBS_SHAPE_GAUSS = 0, 1
 
 
 _lib = None
@@ -213,7 +214,7 @@ def mbs_device_create(qms, materials, regions, length, n_cells, bc=(0.0, 0.0), j
 
 
 def mbs_scenario(device: Device, dt=0.0, courant=1.0, t_end=0.0, n_steps=0, sources=(), probes=()) -> Scenario:
-    sarr = (_Source * max(1, len(sources)))(*[_Source(s.kind, s.cell, s.e0, s.tau, s.t0, s.omega, s.phase)
+    sarr = (_Source * max(1, len(sources)))(*[_Source(s.kind, s.cell, s.e0, s.tau, s.t0, s.omega, s.phase, getattr(s, 'shape', 0))
                                               for s in sources])
     parr = (_Probe * max(1, len(probes)))(*[_Probe(p.cell, p.quantity, p.i, p.j) for p in probes])
     h = C.c_void_p()
@@ -325,7 +326,7 @@ class Cells:
 def mbs_cells_create(qms, dt, n_steps, drives, record_every=1) -> Cells:
     keep = []
     qarr = (_QmDesc * len(qms))(*[_qm_desc(q, keep) for q in qms])
-    darr = (_Source * len(drives))(*[_Source(s.kind, s.cell, s.e0, s.tau, s.t0, s.omega, s.phase) for s in drives])
+    darr = (_Source * len(drives))(*[_Source(s.kind, s.cell, s.e0, s.tau, s.t0, s.omega, s.phase, getattr(s, 'shape', 0)) for s in drives])
     h = C.c_void_p()
     rc = _check(lib().mbs_cells_create(qarr, len(qms), float(dt), int(n_steps), darr, int(record_every),
                                        C.byref(h)))

@@ -780,6 +780,9 @@ void free_scenario(mbs_scenario_s *s) {
 
 double light_speed(const MatDesc &m) { return 1.0 / std::sqrt(kEps0 * m.eps_r * kMu0 * m.mu_r); }
 
+// source envelopes (Sec. 3.1.2, sech_pulse / gaussian_pulse) at x = (t - t0)/tau
+double envelope(int shape, double x) { return shape == MBS_SHAPE_GAUSS ? std::exp(-x * x) : 1.0 / std::cosh(x); }
+
 }  // namespace
 
 int mbs::set_error(int code, const char *msg) { return fail(code, "%s", msg); }
@@ -1060,6 +1063,7 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
   for (int k = 0; k < n_src; ++k) {
     const mbs_source &sr = src[k];
     if (sr.kind < 0 || sr.kind > 2) return fail(MBS_E_INVALID, "source %d: bad kind", k);
+    if (sr.shape != MBS_SHAPE_SECH && sr.shape != MBS_SHAPE_GAUSS) return fail(MBS_E_INVALID, "source %d: bad shape", k);
     if (sr.cell < 2 || sr.cell > nx - 3) return fail(MBS_E_INVALID, "source %d: cell must be in [2, n_cells-3]", k);
     if (!(sr.tau > 0)) return fail(MBS_E_INVALID, "source %d: tau must be > 0", k);
     if (!std::isfinite(sr.e0) || !std::isfinite(sr.tau) || !std::isfinite(sr.t0) || !std::isfinite(sr.omega) ||
@@ -1075,7 +1079,7 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
     const double cs = light_speed(ms), eta_s = std::sqrt(kMu0 * ms.mu_r / (kEps0 * ms.eps_r));
     const double bh = s->emc[dev->cell_mat[sr.cell] * 4 + 1];
     const double ch = h.face >= 0 ? s->emc[dev->cell_mat[h.face] * 4 + 2] : 0.0;
-    auto S = [&](double t) { return sr.e0 / std::cosh((t - sr.t0) / sr.tau) * std::sin(sr.omega * t + sr.phase); };
+    auto S = [&](double t) { return sr.e0 * envelope(sr.shape, (t - sr.t0) / sr.tau) * std::sin(sr.omega * t + sr.phase); };
     for (long long n = 0; n < nt; ++n) {
       const double tn = n * dt;
       if (sr.kind == MBS_SRC_HARD) {
@@ -1931,13 +1935,14 @@ int mbs_cells_create(const mbs_qm_desc *qms, int n_sys, double dt, long long n_s
   c->tab_id.assign(n_sys, 0);
   int status = MBS_OK;
   // drive shapes: systems with the same (tau, t0, omega, phase) share one
-  std::vector<std::array<double, 4>> shapes;
+  std::vector<std::array<double, 5>> shapes;
   for (int s = 0; s < n_sys; ++s) {
     const mbs_source &d = drives[s];
     if (!std::isfinite(d.e0) || !std::isfinite(d.tau) || !std::isfinite(d.t0) || !std::isfinite(d.omega) ||
         !std::isfinite(d.phase) || !(d.tau > 0))
       return fail(MBS_E_INVALID, "system %d: drive parameters must be finite with tau > 0", s);
-    const std::array<double, 4> k{d.tau, d.t0, d.omega, d.phase};
+    if (d.shape != MBS_SHAPE_SECH && d.shape != MBS_SHAPE_GAUSS) return fail(MBS_E_INVALID, "system %d: bad shape", s);
+    const std::array<double, 5> k{d.tau, d.t0, d.omega, d.phase, (double)d.shape};
     int id = -1;
     for (size_t j = 0; j < shapes.size() && id < 0; ++j)
       if (shapes[j] == k) id = (int)j;
@@ -1949,12 +1954,13 @@ int mbs_cells_create(const mbs_qm_desc *qms, int n_sys, double dt, long long n_s
     c->amp[s] = d.e0;
   }
   c->n_tab = (int)shapes.size();
-  // E^n = e0 sech((t_n - t0)/tau) sin(omega t_n + phase), t_n = n dt; E^0 = 0
+  // E^n = e0 envelope((t_n - t0)/tau) sin(omega t_n + phase), t_n = n dt; E^0 = 0
   c->tab.assign((size_t)c->n_tab * n_steps, 0.0);
   for (int j = 0; j < c->n_tab; ++j)
     for (long long n = 1; n < n_steps; ++n) {
       const double t = (double)n * dt;
-      c->tab[(size_t)j * n_steps + n] = std::sin(shapes[j][2] * t + shapes[j][3]) / std::cosh((t - shapes[j][1]) / shapes[j][0]);
+      c->tab[(size_t)j * n_steps + n] =
+          std::sin(shapes[j][2] * t + shapes[j][3]) * envelope((int)shapes[j][4], (t - shapes[j][1]) / shapes[j][0]);
     }
   std::vector<int> codes(n_sys, MBS_OK);
   std::vector<std::string> msgs(n_sys);

@@ -199,3 +199,17 @@ def test_wide_tiles_reject_depths_outside_the_light_cone():
         mbs.mbs_solve([sc], "fp32", "tiled", tile_steps=28, wide_tiles=True)
     assert e.value.status == mbs.MBS_E_INVALID
     mbs.mbs_solve([sc], "fp32", "tiled", tile_steps=26, wide_tiles=True)
+
+
+@pytest.mark.parametrize("n_levels", [2, 3, 4, 5, 6])
+def test_anharmonic_ladder_gaussian_source(n_levels):
+    """The anharmonic ladder of the paper's six-level example for N = 2..6
+    (FP32 CUDA-core tiles for N = 2, 3, tensor-core tiles for N >= 4) driven
+    by a Gaussian-envelope source, against the oracle; FP64 plain to 1e-10."""
+    p = W.ladder_anharmonic(n_levels, n_cells=1_500, n_steps=2_500, t0=200e-15, tau=40e-15)
+    ref = oracle.run(p)["records"]
+    got = mbs.run(p, precision="fp32")
+    assert trace_errors(p, got["records"], ref).max() <= TOL32
+    got64 = mbs.run(p, precision="fp64", algo="plain")
+    for k in range(len(p.probes)):
+        assert rel_l2(got64["records"][k], ref[k]) <= 1e-10, k

@@ -34,7 +34,7 @@ def test_exports_every_declared_symbol():
     for n in sorted(names):
         assert hasattr(L, n), n
     assert names == set(mbs.EXPORTS)
-    assert mbs.mbs_abi_version() == 1
+    assert mbs.mbs_abi_version() == 2
 
 
 def _tiny_problem(**kw):

@@ -349,6 +349,24 @@ def test_vacuum_translation_exact():
     assert np.abs(r["records"][-2:]).max() <= 1e-13 * s.e0
 
 
+def test_vacuum_translation_gaussian_source():
+    """The same exact translation for a Gaussian-envelope source (class
+    gaussian_pulse, Sec. 3.1.2): the oracle's waveform equals the envelope
+    exp(-((t - t0)/tau)^2) written out independently here."""
+    p = _vacuum()
+    s0 = p.sources[0]
+    s = W.Source(s0.kind, s0.cell, s0.e0, 2 * s0.tau, s0.t0 + 20e-15, s0.omega, 0.3, W.SHAPE_GAUSS)
+    p.sources = [s]
+    cells = [2, 700, 2047]
+    p.probes = [W.Probe(c, W.Q_E) for c in cells]
+    r = oracle.run(p)
+    n = np.arange(r["nt"])
+    for k, c in enumerate(cells):
+        t = (n + 1 - (c - 2)) * r["dt"]
+        ref = np.where(t >= 0, s.e0 * np.exp(-((t - s.t0) / s.tau) ** 2) * np.sin(s.omega * t + s.phase), 0.0)
+        assert np.abs(r["records"][k] - ref).max() <= 1e-13 * s.e0
+
+
 def test_pec_reflection_exact():
     """R = 1: the right end reflects the pulse with E -> -E about the last
     cell centre."""

@@ -45,6 +45,8 @@ C0 = 1.0 / math.sqrt(EPS0 * MU0)
 SRC_TFSF_RIGHT = 0   # one-way injection of a +x travelling wave at `cell`
 SRC_TFSF_LEFT = 1    # one-way injection of a -x travelling wave at `cell`
 SRC_HARD = 2         # E at `cell` is overwritten by the waveform
+SHAPE_SECH = 0       # source envelope sech((t - t0)/tau)
+SHAPE_GAUSS = 1      # source envelope exp(-((t - t0)/tau)^2)
 
 # probe quantities
 Q_E = 0        # E_z at the cell centre, time level n+1
@@ -103,11 +105,15 @@ class Source:
     t0: float
     omega: float
     phase: float = 0.0
+    shape: int = 0          # SHAPE_SECH or SHAPE_GAUSS
 
     def waveform(self, t):
-        """E0 sech((t - t0)/tau) sin(omega t + phase)  (input definition)."""
+        """E0 envelope((t - t0)/tau) sin(omega t + phase) with the envelope
+        sech(x) or exp(-x^2)  (input definition)."""
         t = np.asarray(t, dtype=np.float64)
-        return self.e0 / np.cosh((t - self.t0) / self.tau) * np.sin(self.omega * t + self.phase)
+        x = (t - self.t0) / self.tau
+        env = np.exp(-x * x) if self.shape == SHAPE_GAUSS else 1.0 / np.cosh(x)
+        return self.e0 * env * np.sin(self.omega * t + self.phase)
 
 
 @dataclass
@@ -379,6 +385,39 @@ def batch_mixed(n_sims=512, seed=4, min_cells=1024, max_cells=65536,
             qm.density *= fd
         out.append(p.replace(name=f"batch_{s}"))
     return out
+
+
+def ladder_anharmonic(n_levels=6, n_cells=8192, n_steps=20_000, omega0=2.0 * math.pi * 1e13, d=1e-29,
+                      density=1e24, decay=1e11, dephase=1e12, area=math.pi, tau=200e-15, t0=1.2e-12,
+                      courant=COURANT_LONG) -> Problem:
+    """The anharmonic ladder of the paper's six-level example, for any N >= 2:
+    E_1 = 0, E_{n+1} = E_n + hbar omega0 [1 - 0.1 (n - 3)], omega0 = 2 pi 1e13
+    rad/s.  The rest is the builder's choice (the paper cites it from
+    elsewhere): nearest-neighbour dipoles mu_{n,n+1} = d sqrt(n), decays
+    |n><n+1| at `decay`, dephasing |n><n| at `dephase`, a Gaussian pulse from
+    the left at omega0 with area `area` on mu_12, 8192 cells of the SIT grid
+    (medium 5-95 %), probes by the usual rule."""
+    n = n_levels
+    en = [0.0]
+    for k in range(1, n):
+        en.append(en[-1] + HBAR * omega0 * (1.0 - 0.1 * (k - 3)))
+    mu = np.zeros((n, n), complex)
+    for k in range(n - 1):
+        mu[k, k + 1] = mu[k + 1, k] = d * math.sqrt(k + 1)
+    ops = [_ketbra(n, k, k + 1) for k in range(n - 1)] + [_ketbra(n, k, k) for k in range(n)]
+    rates = [decay] * (n - 1) + [dephase] * n
+    qm = QM(n, density, np.diag(en).astype(complex), mu, _ketbra(n, 0, 0), np.array(rates), np.array(ops))
+    length, mats, regs = _medium_device(n_cells, DZ_SIT)
+    # area of exp(-x^2) sin envelope: mu E0 tau sqrt(pi) / hbar
+    e0 = area * HBAR / (d * tau * math.sqrt(math.pi))
+    src = Source(SRC_TFSF_RIGHT, SOURCE_CELL, e0, tau, t0, (en[1] - en[0]) / HBAR, 0.0, SHAPE_GAUSS)
+    probes = []
+    for c in rule_probes(SOURCE_CELL, n_cells, n_steps):
+        probes.append(Probe(c, Q_E))
+        if in_medium(c, n_cells):
+            probes += [Probe(c, Q_RHO_RE, k, k) for k in range(n)]
+    return Problem(f"ladder_anharmonic_{n}lvl", [qm], mats, regs, length, n_cells, n_steps=n_steps,
+                   sources=[src], probes=probes, courant=courant)
 
 
 @dataclass
