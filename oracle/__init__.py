@@ -76,7 +76,8 @@ class _Problem(C.Structure):
                 ("jitter", C.c_void_p),
                 ("courant", C.c_double), ("t_end", C.c_double), ("n_steps", C.c_long),
                 ("n_src", C.c_int), ("src", C.POINTER(_Src)),
-                ("n_probe", C.c_int), ("probe", C.POINTER(_Probe))]
+                ("n_probe", C.c_int), ("probe", C.POINTER(_Probe)),
+                ("e_init", C.c_void_p)]
 
 
 def _load():
@@ -192,10 +193,14 @@ def run(problem, n_threads: int = 0, check_invariants: bool = False):
     if problem.jitter is not None:
         jit = np.ascontiguousarray(np.asarray(problem.jitter, np.float64).reshape(-1, 2))
         assert jit.shape[0] == problem.n_cells
+    e_init = getattr(problem, "e_init", None)
+    if e_init is not None:
+        e_init = np.ascontiguousarray(np.asarray(e_init, np.float64))
+        assert e_init.shape == (problem.n_cells,)
     pb = _Problem(len(problem.qms), qms, len(problem.materials), mats, len(problem.regions), regs,
                   float(problem.length), int(problem.n_cells), float(problem.refl_left),
                   float(problem.refl_right), _ptr(jit), float(problem.courant), float(problem.t_end),
-                  int(problem.n_steps), len(problem.sources), srcs, len(problem.probes), prbs)
+                  int(problem.n_steps), len(problem.sources), srcs, len(problem.probes), prbs, _ptr(e_init))
     info = np.zeros(2)
     if lib.orc_grid(C.byref(pb), info.ctypes.data):
         raise ValueError("a cell centre lies in no region")

@@ -29,9 +29,15 @@
  *   - cell-centred grid dz = L/Nx, cell m at (m + 1/2) dz, E and rho at the
  *     centre, H at the faces f = 0..Nx; face f uses the material of cell f;
  *   - dt = C dz / c_max, Nt = ceil(t_end / dt) (dt is not shrunk);
- *   - reflectivity 0 = first-order Mur, 1 = perfect electric conductor;
+ *   - reflectivity 0 = first-order Mur, 1 = perfect electric conductor,
+ *     0 < R < 1: with the amplitude reflection r = -sqrt(R) and M the Mur
+ *     value, E_b^{n+1} = (1 + r) M^{n+1} - r E_b^{n-1} (E_b^{-1} = E_b^0):
+ *     at Courant number 1 in vacuum the arriving wave is E_nb^n less the
+ *     part already reflected, r E_b^{n-1} / (1 + r), and the cell holds
+ *     (1 + r) times it, so r times the arriving wave goes back exactly;
  *   - soft sources are one-way total-field/scattered-field injections;
- *   - rho at n = -1/2 is the initial density matrix; E^0 = H^{-1/2} = 0.
+ *   - rho at n = -1/2 is the initial density matrix; E^0 = the initial field
+ *     (zero unless given; Sec. 2.1 initial conditions), H^{-1/2} = 0.
  *
  * Matrix exponential: Pade [13/13] with scaling and squaring (Higham 2005,
  * "The scaling and squaring method for the matrix exponential revisited").
@@ -84,6 +90,7 @@ typedef struct {
     double courant; double t_end; long n_steps;
     int n_src; const orc_source *src;
     int n_probe; const orc_probe *probe;
+    const double *e_init;  /* nx initial field values [V/m] or NULL (zero) */
 } orc_problem;
 
 enum { SRC_TFSF_RIGHT = 0, SRC_TFSF_LEFT = 1, SRC_HARD = 2 };
@@ -524,6 +531,9 @@ int orc_run(const orc_problem *pb, int n_threads, int check, double *rec, double
     }
 
     double *E = calloc(nx, sizeof(double)), *En = calloc(nx, sizeof(double));
+    if (pb->e_init)
+        for (int m = 0; m < nx; m++) E[m] = pb->e_init[m];
+    double prev_l = E[0], prev_r = E[nx - 1];   /* E_b^{n-1} of the two ends */
     double *H = calloc(nx + 1, sizeof(double)), *pd = calloc(nx, sizeof(double));
     double st_tr = 0.0, st_herm = 0.0, st_min = 1e300;
     int m0 = 0, mN = nx - 1;
@@ -593,11 +603,29 @@ int orc_run(const orc_problem *pb, int n_threads, int check, double *rec, double
             else if (sr->kind == SRC_HARD)
                 En[c] = waveform(sr, tn + dt);
         }
-        /* boundaries: R = 0 first-order Mur, R = 1 perfect conductor */
-        if (pb->refl_l >= 1.0) En[0] = 0.0;
-        else if (nx > 1) En[0] = E[1] + kl * (En[1] - E[0]);
-        if (pb->refl_r >= 1.0) En[nx - 1] = 0.0;
-        else if (nx > 1) En[nx - 1] = E[nx - 2] + kr * (En[nx - 2] - E[nx - 1]);
+        /* boundaries: R = 0 first-order Mur, R = 1 perfect conductor,
+           0 < R < 1 partially reflecting (see the header) */
+        {
+            const double cur_l = E[0], cur_r = E[nx - 1];
+            if (pb->refl_l >= 1.0) En[0] = 0.0;
+            else if (nx > 1) {
+                En[0] = E[1] + kl * (En[1] - E[0]);
+                if (pb->refl_l > 0.0) {
+                    const double r = -sqrt(pb->refl_l);
+                    En[0] = (1.0 + r) * En[0] - r * prev_l;
+                }
+            }
+            if (pb->refl_r >= 1.0) En[nx - 1] = 0.0;
+            else if (nx > 1) {
+                En[nx - 1] = E[nx - 2] + kr * (En[nx - 2] - E[nx - 1]);
+                if (pb->refl_r > 0.0) {
+                    const double r = -sqrt(pb->refl_r);
+                    En[nx - 1] = (1.0 + r) * En[nx - 1] - r * prev_r;
+                }
+            }
+            prev_l = cur_l;
+            prev_r = cur_r;
+        }
         double *tsw = E; E = En; En = tsw;
         /* 5. records */
         for (int k = 0; k < pb->n_probe; k++) {

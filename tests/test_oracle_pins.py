@@ -529,3 +529,54 @@ def test_vtype_weak_drive_stays_near_ground():
     t = (np.arange(nt) + 1) * dt
     p1 = 1.0 / 3.0 + 2.0 / 3.0 * np.exp(-3.0 * 1e10 * t)
     assert np.max(np.abs(traj[:, 0, 0].real - p1)) < 1e-6
+
+
+@pytest.mark.parametrize("R", [0.25, 0.64])
+def test_partial_reflection_exact(R):
+    """0 < R < 1: the boundary cell takes (1 - sqrt R) times its Mur value, so
+    at Courant number 1 in vacuum the right end sends back r = -sqrt(R) times
+    the arriving pulse, mirrored about the last cell centre: the two ends of
+    the rule are Mur (R = 0) and the perfect conductor (R = 1)."""
+    p = _vacuum()
+    p.refl_right = R
+    cells = [2, 500, 1500, 2040, 2047]
+    p.probes = [W.Probe(c, W.Q_E) for c in cells]
+    r = oracle.run(p)
+    n = np.arange(r["nt"])
+    s = p.sources[0]
+    rr = -np.sqrt(R)
+    for k, c in enumerate(cells):
+        a = n + 1 - (c - 2)
+        b = n + 1 - (2 * 2047 - c - 2)
+        ref = np.where(a >= 0, s.waveform(a * r["dt"]), 0.0) + rr * np.where(b >= 0, s.waveform(b * r["dt"]), 0.0)
+        if c == 2047:   # the boundary cell itself holds incident + reflected = (1 + r) incident
+            ref = (1 + rr) * np.where(a >= 0, s.waveform(a * r["dt"]), 0.0)
+        assert np.abs(r["records"][k] - ref).max() <= 1e-13 * s.e0, (c, np.abs(r["records"][k] - ref).max())
+
+
+def test_initial_field_energy():
+    """A prescribed initial field E^0 (H^{-1/2} = 0) in vacuum at Courant
+    number 1 with mirrors at both ends: the Yee scheme conserves
+    sum_m (E_m^n)^2 + sum_f Hh_f^{n-1/2} Hh_f^{n+1/2} (Hh = eta0 H), which at
+    n = 0 is sum f^2 -- so the field must enter at E^0 with its full value;
+    the pulse splits into two halves moving apart (equal energy each side)."""
+    p = _vacuum()
+    p.sources = []
+    p.refl_left = p.refl_right = 1.0
+    m = np.arange(p.n_cells)
+    f = 1e6 * np.exp(-((m - 1000.0) / 40.0) ** 2)
+    p.e_init = f
+    p.n_steps, p.t_end = 600, 0.0
+    p.probes = [W.Probe(c, W.Q_E) for c in range(p.n_cells)] + [W.Probe(c, W.Q_H) for c in range(p.n_cells)]
+    r = oracle.run(p)
+    E = r["records"][:p.n_cells]                       # E^{n+1}
+    eta0 = math.sqrt(W.MU0 / W.EPS0)
+    H = r["records"][p.n_cells:] * eta0                # Hh^{n+1/2} on the left faces
+    e0 = np.sum(f ** 2)
+    for n in (100, 300, 599):
+        en = np.sum(E[:, n] ** 2) + np.sum(H[:, n] * H[:, n + 1 if n + 1 < p.n_steps else n])
+        if n + 1 < p.n_steps:
+            assert en == pytest.approx(e0, rel=1e-12), n
+    left, right = np.sum(E[:1000, 400] ** 2), np.sum(E[1001:, 400] ** 2)
+    assert left == pytest.approx(right, rel=1e-6)
+    assert left + right == pytest.approx(0.5 * e0, rel=0.02)   # half the energy is magnetic

@@ -140,6 +140,7 @@ class Problem:
     n_steps: int = 0                          # >0 overrides t_end
     sources: List[Source] = field(default_factory=list)
     probes: List[Probe] = field(default_factory=list)
+    e_init: Optional[np.ndarray] = None      # (n_cells,) initial field E^0 [V/m], or None (zero)
 
     @property
     def dz(self) -> float:
