@@ -94,9 +94,13 @@ typedef struct { double eps_r, mu_r, sigma, overlap; int qm; } mbs_material;
 /* Region [x_start, x_end) [m] made of material `material` (Sec. 3.1.1). */
 typedef struct { int material; double x_start, x_end; } mbs_region;
 
-/* Reflectivity of the left and right domain ends (Sec. 2.1): 0 = absorbing
- * (first-order Mur), 1 = perfect mirror (E = 0).  Other values are rejected
- * with MBS_E_INVALID. */
+/* Power reflectivity R of the left and right domain ends (Sec. 2.1):
+ * 0 = absorbing (first-order Mur), 1 = perfect mirror (E = 0),
+ * 0 < R < 1 = partially reflecting facet: with the amplitude reflection
+ * r = -sqrt(R) and M the Mur value, the end cell takes
+ * E_b^{n+1} = (1 + r) M^{n+1} - r E_b^{n-1} (E_b^{-1} = E_b^0), which at
+ * Courant number 1 in vacuum sends back exactly r times the arriving wave.
+ * Values outside [0, 1] are rejected with MBS_E_INVALID. */
 typedef struct { double refl_left, refl_right; } mbs_bc;
 
 /* Create a device.  per_cell_jitter (optional, NULL = none) holds
@@ -211,6 +215,12 @@ int mbs_solve(mbs_scenario_t *batch, int n_scen, const mbs_opts *opts, void *cud
  * out == NULL only *n_written is set (the required count).  Returns
  * MBS_E_INVALID if cap is too small, MBS_E_STATE before the first solve. */
 int mbs_fetch_records(mbs_scenario_t s, int probe, double *out, size_t cap, size_t *n_written);
+
+/* Initial field E^0 of the scenario (Sec. 2.1 initial conditions), one
+ * value per cell [V/m], copied; e0 == NULL restores the default zero field.
+ * H^{-1/2} stays zero.  Used by every later solve.  n must equal n_cells;
+ * non-finite values are rejected. */
+int mbs_scenario_set_field(mbs_scenario_t s, const double *e0, size_t n);
 
 /* Grid facts of a scenario: dt [s], dz [m], number of steps. */
 int mbs_scenario_info(mbs_scenario_t s, double *dt, double *dz, long long *n_steps);

@@ -81,7 +81,8 @@ _lib = None
 EXPORTS = ["mbs_device_create", "mbs_device_destroy", "mbs_device_propagators", "mbs_scenario",
            "mbs_scenario_destroy", "mbs_scenario_info", "mbs_scenario_stats", "mbs_scenario_counters", "mbs_solve",
            "mbs_fetch_records", "mbs_last_error", "mbs_abi_version", "mbs_check_rho_static", "mbs_scenario_tile",
-           "mbs_cells_create", "mbs_cells_solve", "mbs_cells_fetch", "mbs_cells_stats", "mbs_cells_destroy"]
+           "mbs_cells_create", "mbs_cells_solve", "mbs_cells_fetch", "mbs_cells_stats", "mbs_cells_destroy",
+           "mbs_scenario_set_field"]
 
 
 def lib():
@@ -104,6 +105,7 @@ def lib():
         L.mbs_scenario_stats.argtypes = [vp, C.POINTER(d), C.POINTER(d), C.POINTER(ll)]
         L.mbs_scenario_counters.argtypes = [vp, C.POINTER(ll), C.POINTER(ll), C.POINTER(ll)]
         L.mbs_scenario_tile.argtypes = [vp, C.POINTER(i)]
+        L.mbs_scenario_set_field.argtypes = [vp, vp, C.c_size_t]
         L.mbs_cells_create.argtypes = [C.POINTER(_QmDesc), i, d, ll, C.POINTER(_Source), i, C.POINTER(vp)]
         L.mbs_cells_solve.argtypes = [vp, i, vp]
         L.mbs_cells_fetch.argtypes = [vp, i, vp, C.c_size_t, C.POINTER(C.c_size_t)]
@@ -262,6 +264,14 @@ def mbs_scenario_stats(scenario: Scenario):
     return dict(max_trace_dev=tr.value, min_eig=mn.value, n_steps=nt.value)
 
 
+def mbs_scenario_set_field(scenario: Scenario, e0) -> int:
+    """Initial field E^0 [V/m] per cell (None: zero)."""
+    if e0 is None:
+        return _check(lib().mbs_scenario_set_field(scenario.handle, None, 0))
+    buf = np.ascontiguousarray(np.asarray(e0, np.float64))
+    return _check(lib().mbs_scenario_set_field(scenario.handle, buf.ctypes.data, buf.size))
+
+
 def mbs_scenario_tile(scenario: Scenario) -> int:
     t = C.c_int()
     _check(lib().mbs_scenario_tile(scenario.handle, C.byref(t)))
@@ -365,8 +375,11 @@ def device_from_problem(p) -> Device:
 
 
 def scenario_from_problem(dev: Device, p, courant=None) -> Scenario:
-    return mbs_scenario(dev, 0.0, p.courant if courant is None else courant, p.t_end, p.n_steps,
-                        p.sources, p.probes)
+    sc = mbs_scenario(dev, 0.0, p.courant if courant is None else courant, p.t_end, p.n_steps,
+                      p.sources, p.probes)
+    if getattr(p, "e_init", None) is not None:
+        mbs_scenario_set_field(sc, p.e_init)
+    return sc
 
 
 def run(p, precision="fp32", algo="auto", tile_steps=0, check_every=0, stream=None, **flags):

@@ -398,9 +398,11 @@ __device__ __forceinline__ void ff_add(float &h, float &l, float a, float b) {
 }
 
 // (h, l) += (a, b) without renormalising: h takes the rounded sum of the
-// high words, l collects the exact rounding error and the low words.  The
-// pair stays exact; |l| grows by at most an ulp of h per update, and the
-// tiled kernel renormalises once per tile.
+// high words, l collects the exact rounding error and the low words, and the
+// tiled kernels renormalise once per tile.  The pair stays exact, but between
+// renormalisations l may hold a sizeable part of the value (the coupling and
+// loss terms enter through b), so every product with the field must take
+// h + l, not h alone.
 __device__ __forceinline__ void ff_add_lazy(float &h, float &l, float a, float b) {
   float s, e;
   two_sum(h, a, s, e);
@@ -467,6 +469,24 @@ __device__ __forceinline__ void fld_add(real &fh, real &fl, real h, real l) {
 template <typename real>
 __device__ __forceinline__ real fld_val(real h, real l) {
   return sizeof(real) == 8 ? h : h + l;
+}
+
+// Partially reflecting end (reflectivity 0 < R < 1, amplitude reflection
+// r = -sqrt R): the boundary cell holds (1 + r) M - r P = M + r (M - P) with
+// M its first-order Mur value (in e) and P its field two steps back; at
+// Courant number 1 in vacuum this sends back exactly r times the arriving wave.
+template <typename real>
+__device__ __forceinline__ void partial_reflect(real &eh, real &el, real r, real ph, real pl) {
+  if constexpr (sizeof(real) == 8) {
+    eh += r * (eh - ph);
+  } else {
+    float dh, de;
+    two_sum(eh, -ph, dh, de);
+    const float dl = de + (el - pl);
+    float qh, qe;
+    two_prod(r, dh, qh, qe);
+    ff_add(eh, el, qh, qe + r * dl);
+  }
 }
 
 template <typename real>
@@ -591,6 +611,8 @@ __global__ void k_plain_b(const Args a, long long n, int cur) {
       el = FF ? Elo[a.off + nb] : real(0);
       fld_axpy_diff<real>(eh, el, real(left ? a.kmur_l : a.kmur_r), nh, nl, E[idx], FF ? Elo[idx] : real(0),
                           real(0));
+      if ((left ? a.bc_l : a.bc_r) == 2)   // E_b^{n-1}: this thread's output cell still holds it
+        partial_reflect<real>(eh, el, real(left ? a.r_l : a.r_r), En[idx], FF ? Eln[idx] : real(0));
     }
   }
   En[idx] = eh;
@@ -796,6 +818,16 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
   real *rec = reinterpret_cast<real *>(a.rec);
   const real *pcoef = reinterpret_cast<const real *>(a.pr_coef);
 
+  // E_b^{n-1} of the two ends (partially reflecting ends), from the previous launch
+  real pvl_h = real(0), pvl_l = real(0), pvr_h = real(0), pvr_l = real(0);
+  if (any_bnd) {
+    const real *bp = reinterpret_cast<const real *>(a.bprev[cur]);
+    pvl_h = bp[0];
+    pvl_l = bp[1];
+    pvr_h = bp[2];
+    pvr_l = bp[3];
+  }
+
   // E of each warp's last cell, for the next warp's first face
   if (lane == 31) {
     s_x[wib * 4 + 0] = E[R - 1];
@@ -925,7 +957,7 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
 #pragma unroll
       for (int j = 0; j < R; ++j)
         fld_axpy_diff<real, true>(E[j], El[j], cb[j], j < R - 1 ? H[j + 1] : hrh, j < R - 1 ? Hl[j + 1] : hrl, H[j],
-                                  Hl[j], ca[j] * E[j] - pw[j]);
+                                  Hl[j], ca[j] * fld_val<real>(E[j], El[j]) - pw[j]);
     }
     if (any_src) {
       for (int s = 0; s < a.n_src; ++s) {
@@ -957,12 +989,22 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
         if (lft || rgt) {
           const real nh = lft ? (j < R - 1 ? E[j + 1] : r_nh) : (j ? E[j - 1] : l_nh);
           const real nl = lft ? (j < R - 1 ? El[j + 1] : r_nl) : (j ? El[j - 1] : l_nl);
-          if ((lft ? a.bc_l : a.bc_r) == 1) {
+          const int bc = lft ? a.bc_l : a.bc_r;
+          if (bc == 1) {
             Bh[j] = Bl[j] = real(0);
           } else {
             Bh[j] = no_h;
             Bl[j] = no_l;
             fld_axpy_diff<real>(Bh[j], Bl[j], real(lft ? a.kmur_l : a.kmur_r), nh, nl, bo_h, bo_l, real(0));
+            if (bc == 2) partial_reflect<real>(Bh[j], Bl[j], real(lft ? a.r_l : a.r_r), lft ? pvl_h : pvr_h,
+                                               lft ? pvl_l : pvr_l);
+          }
+          if (lft) {   // E_b^n becomes the next step's E_b^{n-1}
+            pvl_h = bo_h;
+            pvl_l = bo_l;
+          } else {
+            pvr_h = bo_h;
+            pvr_l = bo_l;
           }
         }
       }
@@ -989,6 +1031,20 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
 
   // ---- write back the owned cells (never past the last cell)
   if (!owned) return;
+  if (any_bnd) {   // E_b^{n-1} for the next launch, by the owners of the end cells
+    real *bp = reinterpret_cast<real *>(a.bprev[cur ^ 1]);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      if (g0 + j == 0) {
+        bp[0] = pvl_h;
+        bp[1] = pvl_l;
+      }
+      if (g0 + j == a.nx - 1) {
+        bp[2] = pvr_h;
+        bp[3] = pvr_l;
+      }
+    }
+  }
   if constexpr (FF) {
 #pragma unroll
     for (int j = 0; j < R; ++j) {

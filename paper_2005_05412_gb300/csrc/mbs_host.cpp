@@ -378,7 +378,8 @@ struct mbs_device_s {
   std::vector<MatDesc> mats;
   int nx = 0;
   double length = 0, dz = 0;
-  int bc_l = 0, bc_r = 0;
+  int bc_l = 0, bc_r = 0;   // 0 Mur, 1 mirror, 2 partial
+  double r_l = 0, r_r = 0;  // amplitude reflections -sqrt(R)
   std::vector<uint8_t> cell_mat;   // [nx]
   std::vector<double> jitter;      // [nx][2] or empty
   int N = 0;                       // common level count of the media (0: none)
@@ -395,6 +396,7 @@ struct Bundle {  // device buffers of one precision
   void *E[2] = {}, *H[2] = {}, *El[2] = {}, *Hl[2] = {}, *D[2] = {}, *C[2] = {}, *pd = nullptr, *Dinit = nullptr;
   void *emc = nullptr, *qpar = nullptr, *pcell = nullptr, *pcell2 = nullptr, *pr_coef = nullptr, *rec = nullptr;
   float *tcw = nullptr;
+  void *bprev[2] = {};   // E_b^{n-1} of the two ends at a launch boundary: [left hi, left lo, right hi, right lo]
   std::vector<void *> src_tabs;
 };
 
@@ -408,6 +410,10 @@ struct mbs_scenario_s {
   // FP64 master copies
   std::vector<double> emc, qpar, pcell, pcell2, Dinit, pr_coef, zref;
   std::vector<float> tcw;  // tensor-core tiles' constant table (N >= 4, one medium)
+  std::vector<double> e_init;  // initial field E^0 [nx] (empty: zero)
+  // host staging of the asynchronous reset copies (kept alive until the next reset)
+  std::vector<float> e_init_f, bprev_init_f = std::vector<float>(4);
+  std::vector<double> bprev_init_d = std::vector<double>(4);
   bool has_b2 = false;   // structured two-level rows available (pcell2)
 
   std::vector<int> qslot, pr_cell, pr_q;
@@ -668,6 +674,8 @@ void free_bundle(Bundle &b) {
   cudaFree(b.pr_coef);
   cudaFree(b.rec);
   cudaFree(b.tcw);
+  cudaFree(b.bprev[0]);
+  cudaFree(b.bprev[1]);
   for (void *p : b.src_tabs) cudaFree(p);
   b = Bundle();
 }
@@ -691,6 +699,8 @@ int ensure_bundle(mbs_scenario_s *s, int prec) {
     if ((e = cudaMalloc(&b.C[i], row * std::max(K, 1))) != cudaSuccess) return cuda_fail(e, "cudaMalloc C");
   }
   if ((e = cudaMalloc(&b.pd, row)) != cudaSuccess) return cuda_fail(e, "cudaMalloc pd");
+  for (int i = 0; i < 2; ++i)
+    if ((e = cudaMalloc(&b.bprev[i], 4 * rb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc bprev");
   int rc;
   if ((rc = upload(s->Dinit, &b.Dinit, prec))) return rc;
   if ((rc = upload(s->emc, &b.emc, prec))) return rc;
@@ -753,6 +763,10 @@ mbs::Args make_args(mbs_scenario_s *s, int prec) {
   }
   a.bc_l = s->dev->bc_l;
   a.bc_r = s->dev->bc_r;
+  a.r_l = s->dev->r_l;
+  a.r_r = s->dev->r_r;
+  a.bprev[0] = b.bprev[0];
+  a.bprev[1] = b.bprev[1];
   a.kmur_l = s->kmur_l;
   a.kmur_r = s->kmur_r;
   a.n_probe = (int)s->pr_cell.size();
@@ -805,15 +819,18 @@ int mbs_device_create(const mbs_qm_desc *qms, int n_qm, const mbs_material *mats
   if (n_regions < 1 || !regions) return fail(MBS_E_INVALID, "need at least one region");
   if (!(length > 0) || n_cells < 8) return fail(MBS_E_INVALID, "need length > 0 and n_cells >= 8");
   if (n_cells > (1 << 30)) return fail(MBS_E_INVALID, "n_cells too large");
-  auto refl = [](double r) { return r == 0.0 ? 0 : (r == 1.0 ? 1 : -1); };
+  // 0: absorbing (first-order Mur), 1: mirror, 2: partially reflecting
+  auto refl = [](double r) { return r == 0.0 ? 0 : (r == 1.0 ? 1 : (r > 0.0 && r < 1.0 ? 2 : -1)); };
   if (refl(bc.refl_left) < 0 || refl(bc.refl_right) < 0)
-    return fail(MBS_E_INVALID, "reflectivity must be 0 (absorbing) or 1 (mirror)");
+    return fail(MBS_E_INVALID, "reflectivity must be in [0, 1]");
   auto dev = std::make_unique<mbs_device_s>();
   dev->nx = n_cells;
   dev->length = length;
   dev->dz = length / n_cells;
   dev->bc_l = refl(bc.refl_left);
   dev->bc_r = refl(bc.refl_right);
+  dev->r_l = -std::sqrt(bc.refl_left);
+  dev->r_r = -std::sqrt(bc.refl_right);
   int status = MBS_OK;
   for (int i = 0; i < n_qm; ++i) {
     QDesc q;
@@ -1198,6 +1215,42 @@ static int prepare_solve(mbs_scenario_s *s, int prec, cudaStream_t st) {
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(b.pd, 0, row, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_flags, 0, 4 * sizeof(int), st);
+  // the initial field E^0 (also E^{-1}: a static field before the first step)
+  double eb[2] = {0.0, 0.0};
+  if (e == cudaSuccess && !s->e_init.empty()) {
+    const int nx = s->dev->nx;
+    eb[0] = s->e_init[0];
+    eb[1] = s->e_init[nx - 1];
+    if (prec == 0) {
+      for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync((double *)b.E[i] + s->off, s->e_init.data(), nx * sizeof(double), cudaMemcpyHostToDevice, st);
+    } else {
+      s->e_init_f.resize(2 * (size_t)nx);
+      for (int m = 0; m < nx; ++m) {
+        const float hi = (float)s->e_init[m];
+        s->e_init_f[m] = hi;
+        s->e_init_f[nx + m] = (float)(s->e_init[m] - (double)hi);
+      }
+      for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaMemcpyAsync((float *)b.E[i] + s->off, s->e_init_f.data(), nx * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync((float *)b.El[i] + s->off, s->e_init_f.data() + nx, nx * sizeof(float),
+                              cudaMemcpyHostToDevice, st);
+      }
+    }
+  }
+  if (e == cudaSuccess) {
+    if (prec == 0) {
+      s->bprev_init_d = {eb[0], 0.0, eb[1], 0.0};
+      for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(b.bprev[i], s->bprev_init_d.data(), 4 * sizeof(double), cudaMemcpyHostToDevice, st);
+    } else {
+      const float l = (float)eb[0], r = (float)eb[1];
+      s->bprev_init_f = {l, (float)(eb[0] - (double)l), r, (float)(eb[1] - (double)r)};
+      for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(b.bprev[i], s->bprev_init_f.data(), 4 * sizeof(float), cudaMemcpyHostToDevice, st);
+    }
+  }
   if (e != cudaSuccess) return cuda_fail(e, "state reset");
   return MBS_OK;
 }
@@ -1794,6 +1847,20 @@ int mbs_fetch_records(mbs_scenario_t s, int probe, double *out, size_t cap, size
     s->d2h_bytes += (long long)(n * sizeof(float));
     for (size_t i = 0; i < n; ++i) out[i] = scale * (double)f[i];
   }
+  return MBS_OK;
+}
+
+int mbs_scenario_set_field(mbs_scenario_t s, const double *e0, size_t n) {
+  g_err.clear();
+  if (!s) return fail(MBS_E_INVALID, "scenario is NULL");
+  if (!e0) {
+    s->e_init.clear();
+    return MBS_OK;
+  }
+  if (n != (size_t)s->dev->nx) return fail(MBS_E_INVALID, "the initial field needs n_cells = %d values", s->dev->nx);
+  for (size_t m = 0; m < n; ++m)
+    if (!std::isfinite(e0[m])) return fail(MBS_E_INVALID, "non-finite initial field at cell %zu", m);
+  s->e_init.assign(e0, e0 + n);
   return MBS_OK;
 }
 

@@ -94,8 +94,10 @@ struct Args {
 
   int n_src;
   SrcDev src[MAXSRC];
-  int bc_l, bc_r;              // 0 = Mur, 1 = PEC
+  int bc_l, bc_r;              // 0 = Mur, 1 = PEC, 2 = partially reflecting
   double kmur_l, kmur_r;
+  double r_l, r_r;             // amplitude reflections -sqrt(R) (bc 2)
+  void *bprev[2];              // ping-pong [left hi, left lo, right hi, right lo]: E_b^{n0-1}
   int n_probe;
   const int *pr_cell;          // [n_probe]
   const int *pr_q;             // [n_probe] quantity

@@ -76,7 +76,8 @@ struct TcShape {
   static constexpr uint32_t OFF_KP = OFF_ZR + ZR4 * 4;
   static constexpr uint32_t OFF_X = OFF_TAB + TAB * 4;
   static constexpr uint32_t OFF_PR = OFF_X + W * 16;
-  static constexpr uint32_t OFF_BAR = OFF_PR + 2 * MAXPROBE * 4;
+  static constexpr uint32_t OFF_PV = OFF_PR + 2 * MAXPROBE * 4;   // E_b^{n-1} of the ends: 4 floats
+  static constexpr uint32_t OFF_BAR = OFF_PV + 16;
   static constexpr uint32_t SMEM = OFF_BAR + 16;
   static_assert(NCH * 16 <= NO, "compensation chunks fit their columns");
   // chunk of the seeded accumulator after which A chunk c (elements 4c..4c+3
@@ -313,6 +314,10 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
   float *rec = reinterpret_cast<float *>(a.rec);
   const float *pcoef = reinterpret_cast<const float *>(a.pr_coef);
 
+  // E_b^{n-1} of the two ends (partially reflecting ends), from the previous
+  // launch; kept in shared memory (only the lanes holding an end use it)
+  float *s_pv = reinterpret_cast<float *>(smem + S::OFF_PV);   // left hi, lo, right hi, lo
+  if (tid < 4) s_pv[tid] = reinterpret_cast<const float *>(a.bprev[cur])[tid];
   if (lane == 31) {
     s_x[wib * 4 + 0] = E;
     s_x[wib * 4 + 1] = El;
@@ -518,7 +523,7 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
         hrh = s_x[(wib + 1) * 4 + 2];
         hrl = s_x[(wib + 1) * 4 + 3];
       }
-      fld_axpy_diff<float, true>(E, El, cb, hrh, hrl, H, Hl, ca * E - pw);
+      fld_axpy_diff<float, true>(E, El, cb, hrh, hrl, H, Hl, ca * fld_val<float>(E, El) - pw);
     }
     if (any_src)
       for (int s = 0; s < a.n_src; ++s)
@@ -539,14 +544,18 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
       const bool lft = g0 == 0, rgt = g0 == a.nx - 1;
       if (lft || rgt) {
         const float nh = lft ? r_nh : l_nh, nl = lft ? r_nl : l_nl;
-        if ((lft ? a.bc_l : a.bc_r) == 1) {
+        const int bc = lft ? a.bc_l : a.bc_r;
+        if (bc == 1) {
           E = El = 0.0f;
         } else {
           float bh = no_h, bl = no_l;
           fld_axpy_diff<float>(bh, bl, float(lft ? a.kmur_l : a.kmur_r), nh, nl, bo_h, bo_l, 0.0f);
+          if (bc == 2) partial_reflect<float>(bh, bl, float(lft ? a.r_l : a.r_r), s_pv[lft ? 0 : 2], s_pv[lft ? 1 : 3]);
           E = bh;
           El = bl;
         }
+        s_pv[lft ? 0 : 2] = bo_h;   // E_b^n becomes the next step's E_b^{n-1}
+        s_pv[lft ? 1 : 3] = bo_l;
       }
     }
     if (probe)
@@ -589,6 +598,17 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
 
   // ---- write back the owned cells
   if (!owned || g0 >= a.nx) return;
+  if (g0 == 0 || g0 == a.nx - 1) {   // E_b^{n-1} for the next launch
+    float *bp = reinterpret_cast<float *>(a.bprev[cur ^ 1]);
+    if (g0 == 0) {
+      bp[0] = s_pv[0];
+      bp[1] = s_pv[1];
+    }
+    if (g0 == a.nx - 1) {
+      bp[2] = s_pv[2];
+      bp[3] = s_pv[3];
+    }
+  }
   ff_renorm(E, El);
   ff_renorm(H, Hl);
   reinterpret_cast<float *>(a.E[cur ^ 1])[base] = E;

@@ -57,8 +57,10 @@ def test_device_validation_errors():
         mbs.mbs_device_create([q], p.materials, p.regions, p.length, p.n_cells)
     with pytest.raises(mbs.MBSError, match="no region"):
         mbs.mbs_device_create(p.qms, p.materials, p.regions[:2], p.length, p.n_cells)
-    with pytest.raises(mbs.MBSError, match="reflectivity"):
-        mbs.mbs_device_create(p.qms, p.materials, p.regions, p.length, p.n_cells, bc=(0.5, 0.0))
+    for bad in ((1.5, 0.0), (0.0, -0.1), (float("nan"), 0.0)):   # 0 <= R <= 1 (partial reflection allowed)
+        with pytest.raises(mbs.MBSError, match="reflectivity"):
+            mbs.mbs_device_create(p.qms, p.materials, p.regions, p.length, p.n_cells, bc=bad)
+    assert mbs.mbs_device_create(p.qms, p.materials, p.regions, p.length, p.n_cells, bc=(0.5, 0.8)).status == 0
     notpsd = W.QM(**{**p.qms[0].__dict__, "rho_init": np.array([[1.2, 0], [0, -0.2]], complex)})
     with pytest.raises(mbs.MBSError, match="positive"):
         mbs.mbs_device_create([notpsd], p.materials, p.regions, p.length, p.n_cells)

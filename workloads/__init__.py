@@ -421,6 +421,47 @@ def ladder_anharmonic(n_levels=6, n_cells=8192, n_steps=20_000, omega0=2.0 * mat
                    sources=[src], probes=probes, courant=courant)
 
 
+def qcl_tzenov(n_cells=8192, n_steps=20_000, seed=7, e_noise=1e2, refl=0.8, courant=COURANT_LONG) -> Problem:
+    """The quantum cascade laser of the paper's frequency-comb example (five
+    levels, parameters of its listing): H0 with diagonal 0.10103, 0.09677,
+    0.09720, 0.08129, 0.07633 eV and tunnelling couplings H_13 = 1.2329 meV,
+    H_23 = -1.3447 meV; one dipole element mu_34 = -e 4 nm; the scattering
+    matrix and pure-dephasing rates (1/0.6 ps for 13, 23; 1/1 ps for the
+    other pairs except 12, which has none) of the listing; n3D = 5.6e21 m^-3;
+    eps_r = 12.96, overlap 0.9, loss alpha0 = 1100 m^-1 (sigma = 2 alpha0
+    eps c); a 5 mm cavity filled with the medium; both facets R = 0.8;
+    rho(0) = |3><3|; a seeded random initial field (normals x e_noise V/m),
+    no source.  Probes: E at both facets and the centre, populations at the
+    centre."""
+    n = 5
+    ev = E_CHARGE
+    h0 = np.diag([0.10103, 0.09677, 0.09720, 0.08129, 0.07633]).astype(complex) * ev
+    h0[0, 2] = h0[2, 0] = 1.2329e-3 * ev
+    h0[1, 2] = h0[2, 1] = -1.3447e-3 * ev
+    mu = np.zeros((n, n), complex)
+    mu[2, 3] = mu[3, 2] = -ev * 4e-9
+    scat = np.array([[0.0, 0.4947, 0.0974, 0.8116, 1.0410],
+                     [0.8245, 0.0, 0.1358, 0.6621, 1.1240],
+                     [0.0229, 0.0469, 0.0, 0.0794, 0.0357],
+                     [0.0047, 0.0029, 0.1252, 0.0, 0.2810],
+                     [0.0049, 0.0049, 0.1101, 0.4949, 0.0]]) * 1e12
+    d_inj, d_xxx = 1.0 / 0.6e-12, 1.0 / 1.0e-12
+    deph = np.array([0.0, d_inj, d_inj] + [d_xxx] * 7)   # order 12, 13, 23, 14, 24, 34, 15, 25, 35, 45
+    rho0 = np.zeros((n, n), complex)
+    rho0[2, 2] = 1.0
+    qm = QM(n, 5.6e21, h0, mu, rho0, scattering=scat, pure_dephasing=deph)
+    eps_r, alpha0 = 12.96, 1100.0
+    sigma = 2.0 * alpha0 * EPS0 * eps_r * C0 / math.sqrt(eps_r)
+    length = 5e-3
+    mats = [Material(eps_r=eps_r, sigma=sigma, overlap=0.9, qm=0)]
+    regs = [Region(0, 0.0, length)]
+    e_init = normals(seed, n_cells) * e_noise
+    mid = n_cells // 2
+    probes = [Probe(0, Q_E), Probe(n_cells - 1, Q_E), Probe(mid, Q_E)] + [Probe(mid, Q_RHO_RE, k, k) for k in range(n)]
+    return Problem("qcl_tzenov", [qm], mats, regs, length, n_cells, refl_left=refl, refl_right=refl,
+                   n_steps=n_steps, probes=probes, courant=courant, e_init=e_init)
+
+
 @dataclass
 class CellBatch:
     """Independent driven quantum systems without propagation (the borderline
