@@ -167,12 +167,13 @@ enum { MBS_ALGO_AUTO = 0,
 
 enum { MBS_SOLVE_ONE_AT_A_TIME = 1,  /* flags: solve batch members one after another */
        MBS_SOLVE_AUTOTUNE = 2,       /* with tile_steps == 0: pick the tile depth by measurement.
-                                        Each candidate depth runs one warm-up and three timed
-                                        launches (CUDA events on cuda_stream) from the current
-                                        state, which is then reset; the fastest per step wins.
-                                        The choice is cached for the process per level count,
-                                        precision, kernel variant and cell / step counts (per
-                                        batch group: its simulations' totals). */
+                                        Each candidate depth runs one warm-up launch and two
+                                        timed rounds of three launches (CUDA events on
+                                        cuda_stream) from the current state, which is then
+                                        reset; the faster round counts and the fastest per step
+                                        wins.  The choice is cached for the process per level
+                                        count, precision, kernel variant and cell / step counts
+                                        (per batch group: its simulations' totals). */
        MBS_SOLVE_GRAPH = 4 };        /* batched tiled solves on a non-NULL stream: the first call
                                         records the whole launch sequence (fork, every round of
                                         every group, join, state checks) into a CUDA graph and
