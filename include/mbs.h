@@ -180,6 +180,12 @@ enum { MBS_SOLVE_ONE_AT_A_TIME = 1,  /* flags: solve batch members one after ano
                                         launches it; later calls with the same scenarios (same
                                         order) and options replay it without rebuilding the task
                                         tables.  Destroying a member scenario frees the graph. */
+enum { MBS_SOLVE_TEST_STALL = 1 << 30 };   /* test of the failure path: the tensor-core tiles
+                                              (N >= 4) issue no MMA, so every block's bounded
+                                              wait on the tensor core expires after about 1 s;
+                                              the blocks free their TMEM and return, and
+                                              mbs_solve returns MBS_E_TIMEOUT with the CUDA
+                                              context intact.  No effect on other kernels. */
 enum { MBS_SOLVE_WIDE_TILES = 8 };   /* N >= 4: tensor-core tiles of 256 cells (two 128-row MMA
                                         groups per block) instead of 128; tile_steps must keep the
                                         absorbing ends inside a tile's light cone for the grid

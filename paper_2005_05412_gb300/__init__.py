@@ -73,6 +73,7 @@ class _Opts(C.Structure):
 
 MBS_SOLVE_ONE_AT_A_TIME, MBS_SOLVE_AUTOTUNE, MBS_SOLVE_GRAPH, MBS_SOLVE_WIDE_TILES = 1, 2, 4, 8
 MBS_SHAPE_SECH, MBS_SHAPE_GAUSS = 0, 1
+MBS_SOLVE_TEST_STALL = 1 << 30
 
 
 _lib = None
@@ -226,7 +227,7 @@ def mbs_scenario(device: Device, dt=0.0, courant=1.0, t_end=0.0, n_steps=0, sour
 
 
 def mbs_solve(scenarios, precision="fp32", algo="auto", tile_steps=0, check_every=0, stream=None,
-              one_at_a_time=False, autotune=False, graph=False, wide_tiles=False):
+              one_at_a_time=False, autotune=False, graph=False, wide_tiles=False, test_stall=False):
     """Run every scenario to its end (a batch advances together unless
     one_at_a_time).  stream: a cudaStream_t handle (int), e.g.
     torch.cuda.current_stream().cuda_stream, or None.  autotune / graph /
@@ -236,7 +237,8 @@ def mbs_solve(scenarios, precision="fp32", algo="auto", tile_steps=0, check_ever
         scenarios = [scenarios]
     arr = (C.c_void_p * len(scenarios))(*[s.handle for s in scenarios])
     flags = ((MBS_SOLVE_ONE_AT_A_TIME if one_at_a_time else 0) | (MBS_SOLVE_AUTOTUNE if autotune else 0)
-             | (MBS_SOLVE_GRAPH if graph else 0) | (MBS_SOLVE_WIDE_TILES if wide_tiles else 0))
+             | (MBS_SOLVE_GRAPH if graph else 0) | (MBS_SOLVE_WIDE_TILES if wide_tiles else 0)
+             | (MBS_SOLVE_TEST_STALL if test_stall else 0))
     o = _Opts(PREC[precision] if isinstance(precision, str) else int(precision),
               ALGO[algo] if isinstance(algo, str) else int(algo), int(tile_steps), int(check_every), flags)
     return _check(lib().mbs_solve(arr, len(scenarios), C.byref(o), None if stream is None else C.c_void_p(int(stream))))

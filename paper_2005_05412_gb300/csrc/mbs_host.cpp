@@ -1449,6 +1449,7 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
   mbs::Args a = make_args(s, prec);
   int algo = o.algo == MBS_ALGO_AUTO ? default_algo(s, prec) : o.algo;
   s->tc_cells = (o.flags & MBS_SOLVE_WIDE_TILES) ? 256 : 128;
+  a.test_stall = (o.flags & MBS_SOLVE_TEST_STALL) ? 1 : 0;
   int T = o.tile_steps > 0 ? o.tile_steps : default_tile_steps(s->N, s->tc_cells);
   const int chk = o.check_every > 0 ? o.check_every : 0;
   int cur = 0;

@@ -104,7 +104,9 @@ struct Args {
   const void *pr_coef;         // [n_probe][K+1]: rho probes h_K, h0
   const float *tcw;            // tensor-core tiles: weight table (tc_weight_table) or null
   void *rec;                   // [n_probe][nt]
-  int *flags;                  // [4] device status words
+  int *flags;                  // [4] device status words: [0] non-finite state, [1] a bounded wait gave up
+  int test_stall;              // test of the failure path: the tensor-core tiles issue no MMA, so their
+                               // first bounded wait expires (about 1 s) and the solve reports a timeout
 };
 
 // Batched single-cell solver (mbs_cells.cu): one thread per driven system.

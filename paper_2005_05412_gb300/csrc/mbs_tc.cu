@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
     }
     tc_fence_before();
     __syncthreads();   // operands written; H of the warp edges published
-    if (tid == 0) {
+    if (tid == 0 && !a.test_stall) {
       tc_fence_after();
       const uint64_t dA_hi = umma_desc(sA_hi, S::LBO_A, S::SBO), dA_lo = umma_desc(sA_lo, S::LBO_A, S::SBO);
       const uint64_t dB_hi = umma_desc(sB_hi, S::LBO_B, S::SBO), dB_lo = umma_desc(sB_lo, S::LBO_B, S::SBO);

@@ -213,3 +213,24 @@ def test_anharmonic_ladder_gaussian_source(n_levels):
     got64 = mbs.run(p, precision="fp64", algo="plain")
     for k in range(len(p.probes)):
         assert rel_l2(got64["records"][k], ref[k]) <= 1e-10, k
+
+
+def test_tensor_core_wait_timeout_is_a_status():
+    """Failure detection without a GPU fault: every wait on the tensor core is
+    bounded.  With the test flag the tiles issue no MMA, so each block's wait
+    on its MMA barrier runs out after about 1 s; the blocks free their TMEM
+    and return, mbs_solve reports MBS_E_TIMEOUT, and the CUDA context stays
+    usable (the next solve of the same scenario is correct)."""
+    import time
+    p = ladder(6, 300, 8)
+    dev = mbs.device_from_problem(p)
+    sc = mbs.scenario_from_problem(dev, p)
+    t0 = time.time()
+    with pytest.raises(mbs.MBSError) as e:
+        mbs.mbs_solve([sc], "fp32", "tiled", tile_steps=8, test_stall=True)
+    assert e.value.status == mbs.MBS_E_TIMEOUT
+    assert time.time() - t0 < 60
+    mbs.mbs_solve([sc], "fp32", "tiled", tile_steps=8)
+    got = np.stack([mbs.mbs_fetch_records(sc, k) for k in range(len(p.probes))])
+    ref = mbs.run(p, precision="fp64", algo="plain")["records"]
+    assert trace_errors(p, got, ref).max() <= TOL32
