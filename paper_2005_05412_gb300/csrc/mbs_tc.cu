@@ -23,7 +23,7 @@
 //   * the threads read their row back (tcgen05.ld), add the whole increment
 //     to the deviation with Kahan compensation, and finish the field update.
 //
-// The tensor-core error is that of the 3xTF32 split (~2^-22 relative per
+// The tensor-core error is that of the 3xTF32 split (~2^-21 relative per
 // product), below the FP32 rounding of the state that the compensated sums
 // already absorb.  Every wait on the tensor core is bounded: on timeout the
 // block raises flags[1] (MBS_E_TIMEOUT on the host), frees its TMEM and
@@ -190,34 +190,11 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// sin x and cos x - 1: Taylor polynomials for |x| <= 1/2 (as sincos_m1), the
-// library routine out of line otherwise, so that the many call sites of one
-// step stay small
-static __device__ __noinline__ void sincos_m1_far(float x, float &s, float &cm1) {
-  float c;
-  sincosf(x, &s, &c);
-  cm1 = c - 1.0f;
-}
-__device__ __forceinline__ void sincos_m1_tc(float x, float &s, float &cm1) {
-  const float t = x * x;
-  float ps = fmaf(t, 1.0f / 362880.0f, -1.0f / 5040.0f);
-  ps = fmaf(t, ps, 1.0f / 120.0f);
-  ps = fmaf(t, ps, -1.0f / 6.0f);
-  ps = fmaf(t, ps, 1.0f);
-  s = x * ps;
-  float pc = fmaf(t, -1.0f / 3628800.0f, 1.0f / 40320.0f);
-  pc = fmaf(t, pc, -1.0f / 720.0f);
-  pc = fmaf(t, pc, 1.0f / 24.0f);
-  pc = fmaf(t, pc, -0.5f);
-  cm1 = t * pc;
-  if (fabsf(x) > 0.5f) sincos_m1_far(x, s, cm1);
-}
-
-// round to TF32 (10 explicit mantissa bits, nearest, ties away from zero)
+// round to TF32 (10 explicit mantissa bits, nearest, ties away from zero) by
+// integer arithmetic on the bits: two integer operations that the compiler
+// folds for constant operands
 __device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 __device__ __forceinline__ void sts128(uint32_t addr, float a, float b, float c, float d) {
@@ -331,6 +308,8 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
   // field angles of the pairs (0, k), k = 1..N-1; every other pair's angle
   // is a difference of two of them (theta_jk = theta_0k - theta_0j)
   const float *kap0 = reinterpret_cast<const float *>(smem + S::OFF_KP);
+  float kap_max = 0.0f;   // |theta_0k| <= |E| kap_max
+  for (int k = 0; k < NP; ++k) kap_max = fmaxf(kap_max, fabsf(kap0[k]));
   // this warp's TMEM lanes (warp w reaches lanes 32 (w mod 4) ..) in its row group's columns
   const uint32_t t_row = tmem + ((uint32_t)((wib & 3) * 32) << 16) + (uint32_t)((wib >> 2) * S::GCOLS);
   const uint32_t t_cmp = t_row + S::C_COL;                        // its compensation words
@@ -354,7 +333,10 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
   bool timed_out = false;   // this thread's wait gave up
   int stop = 0;             // some thread's wait gave up (block-uniform)
 
-  // A operand chunk c of this cell's row: [u, 1, 0...] elements 4c..4c+3 as TF32 hi and lo
+  // A operand chunk c of this cell's row: [u, 1, 0...] elements 4c..4c+3 as
+  // TF32 hi and lo.  hi = u rounded to TF32; lo = u - hi is exact in FP32 and
+  // goes to the tensor core unrounded: the MMA uses its leading 19 bits, so
+  // the operand pair represents u to 2^-21 relative (2^-22 if rounded).
   auto put_a = [&](int c, const float (&u)[K]) {
     float h[4], l[4];
 #pragma unroll
@@ -362,7 +344,7 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
       const int j = 4 * c + e;
       const float v = j < K ? u[j] : (j == K ? 1.0f : 0.0f);
       h[e] = to_tf32(v);
-      l[e] = to_tf32(v - h[e]);
+      l[e] = v - h[e];
     }
     const uint32_t off = (uint32_t)c * S::LBO_A + (uint32_t)tid * 16;
     sts128(sA_hi + off, h[0], h[1], h[2], h[3]);
@@ -399,7 +381,10 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
       float sn[N], cm[N];   // sin, cos - 1 of theta_0k (k = 0: zero angle)
       sn[0] = cm[0] = 0.0f;
 #pragma unroll
-      for (int k = 1; k < N; ++k) sincos_m1_tc(kap0[k - 1] * ej, sn[k], cm[k]);
+      for (int k = 1; k < N; ++k) sincos_m1_taylor(kap0[k - 1] * ej, sn[k], cm[k]);
+      if (__any_sync(FULL, fabsf(ej) * kap_max > 0.5f))   // a strong field somewhere in the warp
+        for (int k = 1; k < N; ++k)
+          if (fabsf(kap0[k - 1] * ej) > 0.5f) sincos_m1_far(kap0[k - 1] * ej, sn[k], cm[k]);
       float u[K];
 #pragma unroll
       for (int i = 0; i < NP; ++i) u[i] = d[i];
@@ -445,7 +430,7 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
     }
     tmem_wait_st();
     fence_async_smem();
-    if (probe) {   // rho probes from the operand row (u = hi + lo to ~2^-22)
+    if (probe) {   // rho probes from the operand row (u = hi + lo exactly)
       float u[K];
 #pragma unroll
       for (int c = 0; c < S::CH; ++c) {

@@ -234,3 +234,26 @@ def test_tensor_core_wait_timeout_is_a_status():
     got = np.stack([mbs.mbs_fetch_records(sc, k) for k in range(len(p.probes))])
     ref = mbs.run(p, precision="fp64", algo="plain")["records"]
     assert trace_errors(p, got, ref).max() <= TOL32
+
+
+@pytest.mark.parametrize("n_levels", [2, 3, 6])
+def test_strong_field_wide_rotation_angles(n_levels):
+    """A field so strong that the rotation angle of the widest eigenvalue gap
+    reaches about 2 rad per step: the tiles leave the Taylor range |theta| <=
+    1/2 of their sin / cos - 1 and take the library routine (a warp-uniform
+    branch); FP32 tiles against the oracle, FP64 plain to 1e-10."""
+    p = ladder(n_levels, 400, 600)
+    dt = p.courant * p.dz / W.C0
+    dev = mbs.device_from_problem(p)
+    lam = mbs.mbs_device_propagators(dev, 0, dt, n_levels)["lam"]
+    s = p.sources[0]
+    e0 = 2.0 * W.HBAR / ((lam.max() - lam.min()) * dt)
+    p = p.replace(sources=[W.Source(s.kind, s.cell, e0, s.tau, s.t0, s.omega, s.phase)])
+    ref = oracle.run(p)["records"]
+    e_max = max(np.abs(ref[k]).max() for k, pr in enumerate(p.probes) if pr.quantity == W.Q_E)
+    assert (lam.max() - lam.min()) * e_max * dt / W.HBAR > 1.0
+    got = mbs.run(p, precision="fp32")
+    assert trace_errors(p, got["records"], ref).max() <= TOL32
+    got64 = mbs.run(p, precision="fp64", algo="plain")["records"]
+    for k in range(len(p.probes)):
+        assert rel_l2(got64[k], ref[k]) <= 1e-10, k
