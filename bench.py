@@ -297,16 +297,18 @@ def level_leg(mbs, stream, torch, name, T, pk, clocks, reps=2, fp64_steps=1000):
     t = timed(sc, "fp32", "tiled", T, tune=T == 0)
     launches = mbs.mbs_scenario_counters(sc)["kernel_launches"]
     Teff = mbs.mbs_scenario_tile(sc)
+    cells = mbs.mbs_scenario_tile_cells(sc)
     value = p.n_cells * p.n_steps / t / 1e9
     hbm = pk.get("hbm_gbs") or HBM_FALLBACK
     per_launch = t / max(1, launches)
     out = {"value": round(value, 3), "unit": METRIC,
            "workload": f"{p.name}: {p.n_cells} cells x {p.n_steps} steps, N={n}", "precision": "fp32",
-           "tile_steps": Teff, "tile_choice": "autotuned (MBS_SOLVE_AUTOTUNE)" if T == 0 else "fixed"}
+           "tile_steps": Teff, "tile_cells": cells,
+           "tile_choice": "autotuned (MBS_SOLVE_AUTOTUNE)" if T == 0 else "fixed"}
     hb = {"bound": "hbm", "achieved": round(state_bytes(n) * value, 1), "peak": hbm, "unit": "GB/s",
           "frac": round(state_bytes(n) * value / hbm, 4), "alg_bytes_per_cell_step": state_bytes(n),
           "peak_source": "measured" if pk.get("hbm_gbs") else "fallback", "launch_ms": round(per_launch * 1e3, 5)}
-    prof = load_profile(f"{name}_fp32_T{Teff}")
+    prof = load_profile(f"{name}_fp32_T{Teff}" + ("" if n < 4 or cells == 128 else f"_C{cells}"))
     hb["traffic"] = prof.get("dram_bytes") if prof else None
     if prof and prof.get("warp_inst") and clocks.get("sm_mhz"):
         ach = prof["warp_inst"] / per_launch / 1e9
@@ -321,16 +323,16 @@ def level_leg(mbs, stream, torch, name, T, pk, clocks, reps=2, fp64_steps=1000):
         sh = (n - 1) & 1
         ka = (K + 1 + 7) // 8 * 8
         no = (K + sh + 1 + 15) // 16 * 16
-        own = 128 - 2 * Teff
+        own = cells - 2 * Teff
         bf16 = pk.get("bf16_tflops")
         tf32 = bf16 * 1.1 / 2.25 if bf16 else 1900.0 * 1.1 / 2.25
-        exec_tf = 3 * 2 * no * ka * value * 1e9 * 128 / own / 1e12
+        exec_tf = 3 * 2 * no * ka * value * 1e9 * cells / own / 1e12
         out["tensor"] = {"bound": "tensor", "achieved": round(exec_tf, 1), "peak": round(tf32, 1),
                          "unit": "TFLOP/s", "frac": round(exec_tf / tf32, 4),
                          "useful_tflops": round(2 * K * K * value * 1e9 / 1e12, 2),
                          "peak_source": ("measured bf16 x nominal tf32/bf16 (1.1/2.25)" if bf16
                                          else "fallback bf16 x nominal tf32/bf16"),
-                         "kernel": f"k_tiled_tc<{n}> (tcgen05 kind::tf32, 3xTF32, M=128 N={no} K={ka})"}
+                         "kernel": f"k_tiled_tc<{n},{cells // 128}> (tcgen05 kind::tf32, 3xTF32, M=128 N={no} K={ka})"}
     q = p.replace(n_steps=fp64_steps)
     dq = mbs.device_from_problem(q)
     sq = mbs.scenario_from_problem(dq, q)

@@ -261,6 +261,12 @@ int mbs_device_propagators(mbs_device_t dev, int qm, double dt,
  * path; MBS_E_STATE before the first solve. */
 int mbs_scenario_tile(mbs_scenario_t s, int *tile_steps);
 
+/* Cells per tile of the last solve's tiled launches (each tile owns
+ * tile_cells - 2 tile_steps of them): 512 for N = 2 and 3, 128 or 256 for
+ * the tensor-core tiles of N >= 4 (the autotuner may pick either); 0 for the
+ * plain path; MBS_E_STATE before the first solve. */
+int mbs_scenario_tile_cells(mbs_scenario_t s, int *tile_cells);
+
 /* Transfer and launch counters: bytes copied host -> device by the
  * scenario's creation and its solves so far, bytes copied device -> host by
  * the last solve and the fetches after it, CUDA kernel launches issued by

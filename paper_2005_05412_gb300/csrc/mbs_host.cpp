@@ -1878,6 +1878,15 @@ int mbs_scenario_tile(mbs_scenario_t s, int *tile_steps) {
   return MBS_OK;
 }
 
+int mbs_scenario_tile_cells(mbs_scenario_t s, int *tile_cells) {
+  g_err.clear();
+  if (!s) return fail(MBS_E_INVALID, "scenario is NULL");
+  if (s->solved_prec < 0) return fail(MBS_E_STATE, "no solve has run");
+  if (tile_cells)
+    *tile_cells = s->tile_used == 0 ? 0 : s->N >= 4 ? s->tc_cells : 32 * mbs::tile_warps(s->N) * mbs::tile_lane_cells(s->N);
+  return MBS_OK;
+}
+
 int mbs_scenario_counters(mbs_scenario_t s, long long *h2d_bytes, long long *d2h_bytes, long long *kernel_launches) {
   g_err.clear();
   if (!s) return fail(MBS_E_INVALID, "scenario is NULL");
