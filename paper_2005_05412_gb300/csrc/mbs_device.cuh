@@ -61,8 +61,13 @@ __device__ __forceinline__ void sincos_m1_taylor(float x, float &s, float &cm1) 
 }
 
 // |x| > 1/2 in the tiles: out of line, so that the common path carries no
-// library code
-static __device__ __noinline__ void sincos_m1_far(float x, float &s, float &cm1) { sincos_m1_wide(x, s, cm1); }
+// library code; (sin x, cos x - 1) returned by value, so that the caller's
+// results stay in registers
+static __device__ __noinline__ float2 sincos_m1_far(float x) {
+  float2 r;
+  sincos_m1_wide(x, r.x, r.y);
+  return r;
+}
 
 // sin x and cos x - 1 for any x
 __device__ __forceinline__ void sincos_m1(float x, float &s, float &cm1) {
@@ -112,7 +117,11 @@ __device__ __forceinline__ void sincos_m1_sel(float x, float &s, float &cm1) {
     sincos_m1(x, s, cm1);
   } else {
     sincos_m1_taylor(x, s, cm1);
-    if (ROT == ROT_FAR && fabsf(x) > 0.5f) sincos_m1_far(x, s, cm1);
+    if (ROT == ROT_FAR && fabsf(x) > 0.5f) {
+      const float2 r = sincos_m1_far(x);
+      s = r.x;
+      cm1 = r.y;
+    }
   }
 }
 template <int ROT>

@@ -78,7 +78,7 @@ struct TcShape {
   static constexpr uint32_t OFF_PR = OFF_X + W * 16;
   static constexpr uint32_t OFF_PV = OFF_PR + 2 * MAXPROBE * 4;   // E_b^{n-1} of the ends: 4 floats
   static constexpr uint32_t OFF_BAR = OFF_PV + 16;
-  static constexpr uint32_t SMEM = OFF_BAR + 16;
+  static constexpr uint32_t SMEM = OFF_BAR + 16;   // mbarrier (8 bytes), TMEM address, max |kappa_0k|
   static_assert(NCH * 16 <= NO, "compensation chunks fit their columns");
   // chunk of the seeded accumulator after which A chunk c (elements 4c..4c+3
   // of [u, 1, 0...]) is known; -1: populations and constants only
@@ -175,6 +175,32 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
                  "+r"(r[15])::"memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// two such loads (columns ta.. and tb..) under one wait
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, float (&va)[16], uint32_t tb, float (&vb)[16]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(tb));
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])::"memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    va[i] = __uint_as_float(r[i]);
+    vb[i] = __uint_as_float(r[16 + i]);
+  }
 }
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
@@ -299,6 +325,15 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
     s_x[wib * 4 + 0] = E;
     s_x[wib * 4 + 1] = El;
   }
+  // largest |kappa_0k|: |theta_0k| <= |E| kap_max (kept in shared memory:
+  // registers are full)
+  float *s_kmax = reinterpret_cast<float *>(smem + S::OFF_BAR + 12);
+  if (tid == 0) {
+    const float *kp = reinterpret_cast<const float *>(a.tcw) + (S::OFF_KP - S::OFF_TAB) / 4;
+    float m = 0.0f;
+    for (int k = 0; k < NP; ++k) m = fmaxf(m, fabsf(kp[k]));
+    *s_kmax = m;
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -308,8 +343,6 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
   // field angles of the pairs (0, k), k = 1..N-1; every other pair's angle
   // is a difference of two of them (theta_jk = theta_0k - theta_0j)
   const float *kap0 = reinterpret_cast<const float *>(smem + S::OFF_KP);
-  float kap_max = 0.0f;   // |theta_0k| <= |E| kap_max
-  for (int k = 0; k < NP; ++k) kap_max = fmaxf(kap_max, fabsf(kap0[k]));
   // this warp's TMEM lanes (warp w reaches lanes 32 (w mod 4) ..) in its row group's columns
   const uint32_t t_row = tmem + ((uint32_t)((wib & 3) * 32) << 16) + (uint32_t)((wib >> 2) * S::GCOLS);
   const uint32_t t_cmp = t_row + S::C_COL;                        // its compensation words
@@ -382,9 +415,13 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
       sn[0] = cm[0] = 0.0f;
 #pragma unroll
       for (int k = 1; k < N; ++k) sincos_m1_taylor(kap0[k - 1] * ej, sn[k], cm[k]);
-      if (__any_sync(FULL, fabsf(ej) * kap_max > 0.5f))   // a strong field somewhere in the warp
+      if (__any_sync(FULL, fabsf(ej) * *s_kmax > 0.5f))   // a strong field somewhere in the warp
         for (int k = 1; k < N; ++k)
-          if (fabsf(kap0[k - 1] * ej) > 0.5f) sincos_m1_far(kap0[k - 1] * ej, sn[k], cm[k]);
+          if (fabsf(kap0[k - 1] * ej) > 0.5f) {
+            const float2 r = sincos_m1_far(kap0[k - 1] * ej);
+            sn[k] = r.x;
+            cm[k] = r.y;
+          }
       float u[K];
 #pragma unroll
       for (int i = 0; i < NP; ++i) u[i] = d[i];
@@ -473,11 +510,12 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
 #pragma unroll
     for (int c16 = 0; c16 < S::NO / 16; ++c16) {
       if (16 * c16 > K + SH) break;
-      float acc[16];
-      tmem_ld16(t_row + 16 * c16, acc);
+      float acc[16], cw[16];
+      if (c16 < S::NCH)
+        tmem_ld16x2(t_row + 16 * c16, acc, t_cmp + 16 * c16, cw);
+      else
+        tmem_ld16(t_row + 16 * c16, acc);
       if (c16 < S::NCH) {
-        float cw[16];
-        tmem_ld16(t_cmp + 16 * c16, cw);
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const int i = 16 * c16 + e - SH;
