@@ -714,6 +714,52 @@ __device__ __forceinline__ void st_row<double, 4>(double *p, const double (&v)[4
   reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
 }
 
+// The probes whose cell a tile owns, in probe order, built by warp 0 (one
+// probe per lane, compacted by ballot): key_of(cell) is the key stored for an
+// owned cell (its cell or tile row) and -1 otherwise; s_key[i] | s_pq[i] =
+// key | probe index + 256 quantity, ended by key -1 unless MAXPROBE are here.
+template <class KeyOf>
+__device__ __forceinline__ void build_probe_list(const Args &a, KeyOf key_of, int *s_key, int *s_pq) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  int np = 0;
+  for (int b = 0; b < a.n_probe; b += 32) {
+    const int p = b + lane;
+    const int cell = p < a.n_probe ? a.pr_cell[p] : 0, q = p < a.n_probe ? a.pr_q[p] : 0;
+    const int key = p < a.n_probe ? key_of(cell) : -1;
+    const unsigned m = __ballot_sync(FULL, key >= 0);
+    if (key >= 0) {
+      const int i = np + __popc(m & ((1u << lane) - 1u));
+      s_key[i] = key;
+      s_pq[i] = p + 256 * q;
+    }
+    np += __popc(m);
+  }
+  if (lane == 0 && np < MAXPROBE) s_key[np] = -1;
+}
+
+// rho probes of one lane's probe cells (mask pmask over its R cells g0 ..):
+// the rotated deviations parked in s_u, the list of build_probe_list (keyed
+// by cell).  Out of line: only lanes that hold a probe call it, and its
+// registers stay out of the step's allocation.
+template <typename real, int N, int R>
+static __device__ __noinline__ void rho_probes_lane(const int *s_plc, const int *s_plp, const real *s_u, int g0,
+                                                    unsigned pmask, const real *pcoef, real *rec, long long nt,
+                                                    long long n) {
+  constexpr int K = N * N - 1;
+  for (int j = 0; j < R; ++j)
+    if (pmask & (1u << j)) {
+      real u[K];
+#pragma unroll
+      for (int i = 0; i < K; ++i) u[i] = s_u[j * K + i];
+      for (int k = 0; k < MAXPROBE && s_plc[k] >= 0; ++k)
+        if (s_plc[k] == g0 + j && s_plp[k] >= 512) {
+          const int p = s_plp[k] & 255;
+          rec[(size_t)p * nt + n] = probe_rho<real, N>(pcoef + (size_t)p * (K + 1), u);
+        }
+    }
+}
+
 // Block tile b owns cells [b*own, (b+1)*own), own = 32 W R - 2 T (W warps);
 // lane l of warp w holds cells tb + (32 w + l) R .. + R - 1 with tb = b*own - T
 // (the tile holding the last cell may start 4 or 8 cells earlier).  Reads
@@ -731,7 +777,12 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
   constexpr bool FF = sizeof(real) == 4;
   constexpr bool PERCELL = PM == 1;
   static_assert(PM != 2 || N == 2, "structured rows are two-level");
-  real *s_emc = reinterpret_cast<real *>(smem_raw);
+  // the probes of this tile's owned cells (build_probe_list, keyed by cell),
+  // at a fixed offset, so that a probe lane's step reads a short list
+  // instead of every probe, through constant shared-memory addresses
+  int *s_plc = reinterpret_cast<int *>(smem_raw);
+  int *s_plp = s_plc + MAXPROBE;
+  real *s_emc = reinterpret_cast<real *>(smem_raw + 2 * MAXPROBE * sizeof(int));
   real *s_q = s_emc + a.n_mat_all * 4;
   int *s_slot = reinterpret_cast<int *>(s_q + a.n_slot * a.qstride);
   for (int i = threadIdx.x; i < a.n_mat_all * 4; i += blockDim.x) s_emc[i] = reinterpret_cast<const real *>(a.emc)[i];
@@ -854,12 +905,10 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
   const bool any_bnd = (t_lo <= 0 && 0 < t_hi) || (t_lo <= a.nx - 1 && a.nx - 1 < t_hi);
   // owned cells of this lane (T, lo and own are multiples of R)
   const bool owned = ti0 >= lo && ti0 < lo + own && ti0 < TSPAN - T;
-  unsigned pmask = 0;
-  for (int p = 0; p < a.n_probe; ++p) {
-    const int j = a.pr_cell[p] - g0;
-    if (owned && j >= 0 && j < R) pmask |= 1u << j;
-  }
-  const bool any_probe = __any_sync(FULL, pmask != 0);
+  build_probe_list(a, [&](int c) {
+    const int ti = c - tb;   // tile position of the probe cell
+    return ti >= lo && ti < lo + own && ti < TSPAN - T ? c : -1;
+  }, s_plc, s_plp);
   real *rec = reinterpret_cast<real *>(a.rec);
   const real *pcoef = reinterpret_cast<const real *>(a.pr_coef);
 
@@ -879,6 +928,12 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
     s_x[wib * 4 + 1] = El[R - 1];
   }
   __syncthreads();
+  unsigned pmask = 0;   // this lane's probe cells
+  for (int k = 0; k < MAXPROBE && s_plc[k] >= 0; ++k) {
+    const int j = s_plc[k] - g0;
+    if (j >= 0 && j < R) pmask |= 1u << j;
+  }
+  const bool any_probe = __any_sync(FULL, pmask != 0);
 
 #pragma unroll 1
   for (int t = 0; t < nsteps; ++t) {
@@ -977,18 +1032,7 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
       }
     }
     if (warp_med) {
-      if (any_probe && pmask) {
-#pragma unroll
-        for (int j = 0; j < R; ++j)
-          if (pmask & (1u << j)) {
-            real u[K];
-#pragma unroll
-            for (int i = 0; i < K; ++i) u[i] = s_u[j * K + i];
-            for (int p = 0; p < a.n_probe; ++p)
-              if (a.pr_cell[p] == g0 + j && a.pr_q[p] >= 2)
-                rec[(size_t)p * a.nt + n] = probe_rho<real, N>(pcoef + (size_t)p * (K + 1), u);
-          }
-      }
+      if (any_probe && pmask) rho_probes_lane<real, N, R>(s_plc, s_plp, s_u, g0, pmask, pcoef, rec, a.nt, n);
     }
     // ---- boundary cells: keep E^n of the boundary cell and its neighbour
     real bo_h = real(0), bo_l = real(0), no_h = real(0), no_l = real(0);
@@ -1084,9 +1128,11 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
 #pragma unroll
       for (int j = 0; j < R; ++j)
         if (pmask & (1u << j))
-          for (int p = 0; p < a.n_probe; ++p)
-            if (a.pr_cell[p] == g0 + j && a.pr_q[p] < 2)
-              rec[(size_t)p * a.nt + n] = a.pr_q[p] == 0 ? fld_val<real>(E[j], El[j]) : fld_val<real>(H[j], Hl[j]);
+          for (int k = 0; k < MAXPROBE && s_plc[k] >= 0; ++k)
+            if (s_plc[k] == g0 + j && s_plp[k] < 512) {
+              const int p = s_plp[k] & 255;
+              rec[(size_t)p * a.nt + n] = s_plp[k] < 256 ? fld_val<real>(E[j], El[j]) : fld_val<real>(H[j], Hl[j]);
+            }
     }
     if (lane == 31) {
       s_x[wib * 4 + 0] = E[R - 1];
@@ -1313,7 +1359,8 @@ int plain_step_impl(const Args &a, long long n, int cur, cudaStream_t st) {
 template <typename real, int N, int R>
 size_t tiled_smem(int n_mat_all, int n_slot, int qstride) {
   return sizeof(real) * (n_mat_all * 4 + n_slot * qstride) + ((sizeof(int) * n_mat_all + 15) / 16) * 16 +
-         sizeof(real) * ((size_t)32 * TileGeom<N>::W * R * (N * N - 1) + 4 * TileGeom<N>::W) + 16;
+         sizeof(real) * ((size_t)32 * TileGeom<N>::W * R * (N * N - 1) + 4 * TileGeom<N>::W) + 16 +
+         sizeof(int) * 2 * MAXPROBE;
 }
 
 template <typename real, int N, int R, bool KAHAN, int PM>

@@ -69,8 +69,8 @@ struct TcShape {
   // part padded to whole 16-byte vectors
   static constexpr int ZR4 = (2 * P + 3) / 4 * 4, KP4 = (NP + 3) / 4 * 4;
   static constexpr int TAB = 2 * B_BYTES / 4 + ZR4 + KP4;   // floats
-  // dynamic shared memory: A_hi | A_lo | table | edge slots | probe cells,
-  // quantities | mbarrier, TMEM slot
+  // dynamic shared memory: A_hi | A_lo | table | edge slots | probe rows,
+  // indices | mbarrier, TMEM slot
   static constexpr uint32_t OFF_TAB = 2 * A_BYTES;
   static constexpr uint32_t OFF_ZR = OFF_TAB + 2 * B_BYTES;
   static constexpr uint32_t OFF_KP = OFF_ZR + ZR4 * 4;
@@ -227,6 +227,35 @@ __device__ __forceinline__ void sts128(uint32_t addr, float a, float b, float c,
   asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
 
+// rho probes of warp `wib`'s cells: for each list entry (rows | index + 256
+// quantity, build_probe_list) that is a rho probe of this warp, the warp
+// evaluates the functional together (lane l takes terms l, l + 32) from the
+// probe cell's operand row, u = hi + lo exactly, with the row's constant 1 at
+// element K.  Out of line: only warps that hold a probe call it, and its
+// registers stay out of the step's allocation.
+template <int K, uint32_t LBO_A, uint32_t A_BYTES>
+static __device__ __noinline__ void rho_probes_warp(const int *s_plr, const int *s_plp, const unsigned char *smem,
+                                                    const float *pcoef, float *rec, long long nt, long long n,
+                                                    int wib, int lane) {
+  __syncwarp();   // the warp's operand rows are written
+  for (int k = 0; k < MAXPROBE; ++k) {
+    const int r = s_plr[k];
+    if (r < 0) break;
+    if ((r >> 5) != wib || s_plp[k] < 512) continue;
+    const int p = s_plp[k] & 255;
+    const float *cf = pcoef + (size_t)p * (K + 1);
+    float v = 0.0f;
+    for (int i = lane; i <= K; i += 32) {
+      const uint32_t off = (uint32_t)(i >> 2) * LBO_A + (uint32_t)r * 16 + (uint32_t)(i & 3) * 4;
+      v = fmaf(cf[i], *reinterpret_cast<const float *>(smem + off) + *reinterpret_cast<const float *>(smem + A_BYTES + off),
+               v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == 0) rec[(size_t)p * nt + n] = v;
+  }
+}
+
 // ---------------------------------------------------------------- kernel
 // Tile b owns cells [b*own, (b+1)*own), own = 128 - 2T; thread i holds cell
 // tb + i with tb = b*own - T (the tile holding the last cell may start 4 or 8
@@ -251,7 +280,10 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
   const uint32_t sA_hi = smem_u32(smem), sA_lo = sA_hi + S::A_BYTES;
   const uint32_t sB_hi = sA_lo + S::A_BYTES, sB_lo = sB_hi + S::B_BYTES;
   const float *s_zr = reinterpret_cast<const float *>(smem + S::OFF_ZR);   // zr[2P]
-  const int *s_pc = reinterpret_cast<const int *>(smem + S::OFF_PR);         // probe cells | quantities
+  // the probes of this tile's owned cells (build_probe_list, keyed by tile
+  // row = thread)
+  int *s_plr = reinterpret_cast<int *>(smem + S::OFF_PR);
+  int *s_plp = s_plr + MAXPROBE;
   float *s_x = reinterpret_cast<float *>(smem + S::OFF_X);     // [warp][E hi, E lo, H hi, H lo]
   const uint32_t bar = smem_u32(smem + S::OFF_BAR);
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + S::OFF_BAR + 8);
@@ -266,11 +298,6 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
     for (int r = 0; r < (S::TAB / 4 + S::M - 1) / S::M; ++r) {
       const int i = tid + r * S::M;
       if (i < S::TAB / 4) dst[i] = src[i];
-    }
-    int *pw_ = reinterpret_cast<int *>(smem + S::OFF_PR);
-    if (tid < a.n_probe) {
-      pw_[tid] = a.pr_cell[tid];
-      pw_[MAXPROBE + tid] = a.pr_q[tid];
     }
   }
   fence_async_smem();
@@ -321,6 +348,10 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
   // launch; kept in shared memory (only the lanes holding an end use it)
   float *s_pv = reinterpret_cast<float *>(smem + S::OFF_PV);   // left hi, lo, right hi, lo
   if (tid < 4) s_pv[tid] = reinterpret_cast<const float *>(a.bprev[cur])[tid];
+  build_probe_list(a, [&](int c) {
+    const int r = c - tb;   // tile row of the probe cell
+    return r >= lo && r < lo + own && r < S::M - T ? r : -1;
+  }, s_plr, s_plp);
   if (lane == 31) {
     s_x[wib * 4 + 0] = E;
     s_x[wib * 4 + 1] = El;
@@ -339,7 +370,8 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
   bool probe = false;
-  for (int p = 0; p < a.n_probe; ++p) probe |= owned && s_pc[p] == g0;
+  for (int k = 0; k < MAXPROBE && s_plr[k] >= 0; ++k) probe |= s_plr[k] == tid;
+  const bool warp_probe = __any_sync(FULL, probe);   // some cell of the warp is a probe cell
   // field angles of the pairs (0, k), k = 1..N-1; every other pair's angle
   // is a difference of two of them (theta_jk = theta_0k - theta_0j)
   const float *kap0 = reinterpret_cast<const float *>(smem + S::OFF_KP);
@@ -467,21 +499,8 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
     }
     tmem_wait_st();
     fence_async_smem();
-    if (probe) {   // rho probes from the operand row (u = hi + lo exactly)
-      float u[K];
-#pragma unroll
-      for (int c = 0; c < S::CH; ++c) {
-        const float4 h = *reinterpret_cast<const float4 *>(smem + c * S::LBO_A + tid * 16);
-        const float4 l = *reinterpret_cast<const float4 *>(smem + S::A_BYTES + c * S::LBO_A + tid * 16);
-        const float hv[4] = {h.x, h.y, h.z, h.w}, lv[4] = {l.x, l.y, l.z, l.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (4 * c + e < K) u[4 * c + e] = hv[e] + lv[e];
-      }
-      for (int p = 0; p < a.n_probe; ++p)
-        if (s_pc[p] == g0 && s_pc[MAXPROBE + p] >= 2)
-          rec[(size_t)p * a.nt + n] = probe_rho<float, N>(pcoef + (size_t)p * (K + 1), u);
-    }
+    if (warp_probe)
+      rho_probes_warp<K, S::LBO_A, S::A_BYTES>(s_plr, s_plp, smem, pcoef, rec, a.nt, n, wib, lane);
     tc_fence_before();
     __syncthreads();   // operands written; H of the warp edges published
     if (tid == 0 && !a.test_stall) {
@@ -582,9 +601,9 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
       }
     }
     if (probe)
-      for (int p = 0; p < a.n_probe; ++p)
-        if (s_pc[p] == g0 && s_pc[MAXPROBE + p] < 2)
-          rec[(size_t)p * a.nt + n] = s_pc[MAXPROBE + p] == 0 ? fld_val<float>(E, El) : fld_val<float>(H, Hl);
+      for (int k = 0; k < MAXPROBE && s_plr[k] >= 0; ++k)
+        if (s_plr[k] == tid && s_plp[k] < 512)
+          rec[(size_t)(s_plp[k] & 255) * a.nt + n] = s_plp[k] < 256 ? fld_val<float>(E, El) : fld_val<float>(H, Hl);
     if (lane == 31) {
       s_x[wib * 4 + 0] = E;
       s_x[wib * 4 + 1] = El;
