@@ -176,7 +176,8 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
 
     def solve():
-        mbs.mbs_solve([sc], args.precision, "tiled", tile_steps=T, stream=stream.cuda_stream)
+        mbs.mbs_solve([sc], args.precision, "tiled", tile_steps=T, stream=stream.cuda_stream,
+                      wide_tiles=args.wide_tiles)
 
     for _ in range(args.warmup):
         solve()
@@ -217,7 +218,7 @@ def run_ours(args, rank, world, local):
     per_launch_s = t_local / args.steps / max(1, launches)
     units_per_launch = p.n_cells * T
     achieved = alg_bytes * units_per_launch / per_launch_s / 1e9
-    prof = load_profile(f"{args.workload}_{args.precision}_T{args.tile}")
+    prof = load_profile(f"{args.workload}_{args.precision}_T{args.tile}" + ("_C256" if args.wide_tiles else ""))
     traffic = prof.get("dram_bytes") if prof else None
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm or HBM_FALLBACK, "unit": "GB/s",
             "frac": round(achieved / (hbm or HBM_FALLBACK), 4), "traffic": traffic,
@@ -576,6 +577,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-simulation batch leg")
     ap.add_argument("--nsteps", type=int, default=0, help="override the workload's step count (profiling)")
+    ap.add_argument("--wide-tiles", action="store_true",
+                    help="256-cell tensor-core tiles for the main workload (N >= 4; profiling)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
