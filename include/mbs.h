@@ -261,6 +261,19 @@ int mbs_device_propagators(mbs_device_t dev, int qm, double dt,
  * path; MBS_E_STATE before the first solve. */
 int mbs_scenario_tile(mbs_scenario_t s, int *tile_steps);
 
+/* The tile plan of the tiled kernels, a pure host query (no device work):
+ * whether `tile_steps` steps per launch are valid for tiles of `tile_cells`
+ * cells on an `nx`-cell grid with `n_levels` levels, and how many tiles one
+ * launch runs.  tile_cells = 512 for N = 2 and 3 (tile_steps a multiple of
+ * 4 in [4, 116] for N = 2, [4, 52] for N = 3, any nx); 128 or 256 for the
+ * tensor-core tiles of N = 4..6 (the tile that holds the last cell starts 4
+ * or 8 cells early when that cell would be its first owned cell or start a
+ * warp; tile_steps is valid when the last cell and its neighbour then stay
+ * owned, in one warp and inside the light cone, and so do cell 0 and its
+ * neighbour).  Tile b owns cells [b own, (b + 1) own), own = tile_cells -
+ * 2 tile_steps.  MBS_OK with *n_tiles set, or MBS_E_INVALID. */
+int mbs_tile_plan(int n_levels, int tile_cells, int nx, int tile_steps, int *n_tiles);
+
 /* Cells per tile of the last solve's tiled launches (each tile owns
  * tile_cells - 2 tile_steps of them): 512 for N = 2 and 3, 128 or 256 for
  * the tensor-core tiles of N >= 4 (the autotuner may pick either); 0 for the

@@ -81,7 +81,7 @@ _lib = None
 # every symbol include/mbs.h declares
 EXPORTS = ["mbs_device_create", "mbs_device_destroy", "mbs_device_propagators", "mbs_scenario",
            "mbs_scenario_destroy", "mbs_scenario_info", "mbs_scenario_stats", "mbs_scenario_counters", "mbs_solve",
-           "mbs_fetch_records", "mbs_last_error", "mbs_abi_version", "mbs_check_rho_static", "mbs_scenario_tile", "mbs_scenario_tile_cells",
+           "mbs_fetch_records", "mbs_last_error", "mbs_abi_version", "mbs_check_rho_static", "mbs_scenario_tile", "mbs_scenario_tile_cells", "mbs_tile_plan",
            "mbs_cells_create", "mbs_cells_solve", "mbs_cells_fetch", "mbs_cells_stats", "mbs_cells_destroy",
            "mbs_scenario_set_field"]
 
@@ -277,6 +277,14 @@ def mbs_scenario_set_field(scenario: Scenario, e0) -> int:
 def mbs_scenario_tile(scenario: Scenario) -> int:
     t = C.c_int()
     _check(lib().mbs_scenario_tile(scenario.handle, C.byref(t)))
+    return t.value
+
+
+def mbs_tile_plan(n_levels: int, tile_cells: int, nx: int, tile_steps: int) -> int:
+    """Number of tiles one tiled launch runs; MBSError (MBS_E_INVALID) when
+    tile_steps does not fit (see include/mbs.h)."""
+    t = C.c_int()
+    _check(lib().mbs_tile_plan(int(n_levels), int(tile_cells), int(nx), int(tile_steps), C.byref(t)))
     return t.value
 
 

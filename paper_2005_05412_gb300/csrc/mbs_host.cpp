@@ -1878,6 +1878,27 @@ int mbs_scenario_tile(mbs_scenario_t s, int *tile_steps) {
   return MBS_OK;
 }
 
+int mbs_tile_plan(int n_levels, int tile_cells, int nx, int tile_steps, int *n_tiles) {
+  g_err.clear();
+  const int T = tile_steps;
+  if (n_levels < 2 || n_levels > mbs::NMAX) return fail(MBS_E_INVALID, "n_levels %d outside [2, %d]", n_levels, mbs::NMAX);
+  if (nx < 8) return fail(MBS_E_INVALID, "nx must be at least 8");
+  if (n_levels >= 4) {
+    if (!mbs::tiled_tc_geometry_ok(nx, tile_cells, T))
+      return fail(MBS_E_INVALID, "tile_steps %d does not fit %d-cell tensor-core tiles on a %d-cell grid", T,
+                  tile_cells, nx);
+  } else {
+    if (tile_cells != 32 * mbs::tile_warps(n_levels) * mbs::tile_lane_cells(n_levels))
+      return fail(MBS_E_INVALID, "tiles of N = %d levels hold %d cells", n_levels,
+                  32 * mbs::tile_warps(n_levels) * mbs::tile_lane_cells(n_levels));
+    if (T % 4 != 0 || T < 4 || T > mbs::tile_max_steps(n_levels))
+      return fail(MBS_E_INVALID, "tile_steps must be a multiple of 4 in [4, %d]", mbs::tile_max_steps(n_levels) / 4 * 4);
+  }
+  const int own = tile_cells - 2 * T;
+  if (n_tiles) *n_tiles = (nx + own - 1) / own;
+  return MBS_OK;
+}
+
 int mbs_scenario_tile_cells(mbs_scenario_t s, int *tile_cells) {
   g_err.clear();
   if (!s) return fail(MBS_E_INVALID, "scenario is NULL");
