@@ -49,6 +49,12 @@ def dist_env():
     return rank, world, local
 
 
+def workload_label(p):
+    """The workload named by what it is, identical in both arms' `config`."""
+    return (f"{p.name}: {p.n_cells} cells x {p.n_steps} steps, N={p.qms[0].n_levels}"
+            + (", per-cell jitter" if p.jitter is not None else ""))
+
+
 def workload(name):
     if name == "sit_2lvl_jitter":
         return W.sit_2lvl_jitter()
@@ -241,8 +247,7 @@ def run_ours(args, rank, world, local):
            "warmup": args.warmup, "ms_per_step": round(t_max * 1e3 / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
            "data": "synthetic (seeded)",
-           "config": {"workload": f"{p.name}: {p.n_cells} cells x {p.n_steps} steps, N={n_lv}"
-                                  + (", per-cell jitter" if jit else ""),
+           "config": {"workload": workload_label(p),
                       "precision": args.precision, "algo": "tiled", "tile_steps": T,
                       "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)"},
            "roofline": roof, "clocks": clocks, "gpu_launches": launches * args.steps,
@@ -555,9 +560,7 @@ def run_reference(args, rank, world):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs * 1e3 / args.steps, 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded)",
-           "config": {"workload": f"{p.name}: {p.n_cells} cells x {p.n_steps} steps, N={n_lv}"
-                                  + (", per-cell jitter" if jit else ""),
-                      "precision": "fp64", "algo": "oracle (CPU, OpenMP over cells)"},
+           "config": {"workload": workload_label(p), "precision": "fp64", "algo": "oracle (CPU, OpenMP over cells)"},
            "cpu_baseline": {"value": round(value, 5), "unit": METRIC, "cores": vals[0]["cores"], "kind": "oracle",
                             "sample": vals[0]["sample"]},
            "e2e": {"value": round(value, 5), "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
