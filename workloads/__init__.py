@@ -445,8 +445,8 @@ def qcl_tzenov(n_cells=8192, n_steps=20_000, seed=7, e_noise=1e2, refl=0.8, cour
                      [0.0229, 0.0469, 0.0, 0.0794, 0.0357],
                      [0.0047, 0.0029, 0.1252, 0.0, 0.2810],
                      [0.0049, 0.0049, 0.1101, 0.4949, 0.0]]) * 1e12
-    d_inj, d_xxx = 1.0 / 0.6e-12, 1.0 / 1.0e-12
-    deph = np.array([0.0, d_inj, d_inj] + [d_xxx] * 7)   # order 12, 13, 23, 14, 24, 34, 15, 25, 35, 45
+    d_inj, d_other = 1.0 / 0.6e-12, 1.0 / 1.0e-12
+    deph = np.array([0.0, d_inj, d_inj] + [d_other] * 7)   # order 12, 13, 23, 14, 24, 34, 15, 25, 35, 45
     rho0 = np.zeros((n, n), complex)
     rho0[2, 2] = 1.0
     qm = QM(n, 5.6e21, h0, mu, rho0, scattering=scat, pure_dephasing=deph)
