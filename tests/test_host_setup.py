@@ -192,3 +192,31 @@ def test_reference_state_is_steady_state():
     np.testing.assert_allclose(rho, np.diag([1.0, 0.0]), atol=1e-14)
     assert np.abs(pr["c"]).max() < 1e-15
     assert abs(pr["g0"]) < 1e-6 * 1e-29 * 1e14
+
+
+def test_scenario_validation_errors():
+    """mbs_scenario validates before it touches the device: every bad
+    argument is MBS_E_INVALID with a message, and nothing is allocated."""
+    import dataclasses
+    p = _tiny_problem()
+    dev = mbs.device_from_problem(p)
+    s0 = p.sources[0]
+    cases = [
+        ("probes", p.replace(probes=[W.Probe(3, W.Q_E)] * 65)),
+        ("sources", p.replace(sources=[s0] * 5)),
+        ("cell out of range", p.replace(probes=[W.Probe(p.n_cells, W.Q_E)])),
+        ("bad quantity", p.replace(probes=[W.Probe(3, 7)])),
+        ("without medium", p.replace(probes=[W.Probe(0, W.Q_RHO_RE, 0, 0)])),
+        ("level index", p.replace(probes=[W.Probe(p.n_cells // 2, W.Q_RHO_RE, 0, 2)])),
+        ("bad kind", p.replace(sources=[dataclasses.replace(s0, kind=9)])),
+        ("bad shape", p.replace(sources=[dataclasses.replace(s0, shape=5)])),
+        ("cell must be", p.replace(sources=[dataclasses.replace(s0, cell=1)])),
+        ("tau", p.replace(sources=[dataclasses.replace(s0, tau=0.0)])),
+        ("non-finite", p.replace(sources=[dataclasses.replace(s0, e0=float("nan"))])),
+        ("courant", p.replace(courant=1.5)),
+        ("no time steps", p.replace(n_steps=0, t_end=0.0)),
+    ]
+    for msg, q in cases:
+        with pytest.raises(mbs.MBSError, match=msg) as e:
+            mbs.scenario_from_problem(dev, q)
+        assert e.value.status == mbs.MBS_E_INVALID, msg
