@@ -580,3 +580,53 @@ def test_initial_field_energy():
     left, right = np.sum(E[:1000, 400] ** 2), np.sum(E[1001:, 400] ** 2)
     assert left == pytest.approx(right, rel=1e-6)
     assert left + right == pytest.approx(0.5 * e0, rel=0.02)   # half the energy is magnetic
+
+
+def _two_media(eps_r, sigma=0.0, n_cells=8192, n_steps=10_000, tau=30e-15):
+    """Vacuum on cells [0, n/2), a dielectric (eps_r, sigma, no medium) on
+    [n/2, n); a narrowband sech pulse (omega0 tau = 6) enters from the left."""
+    p = W.sit_2lvl(n_cells=n_cells, t_end=0.0, n_steps=n_steps)
+    p.qms[0].density = 0.0
+    L = p.length
+    p.materials = [W.Material(), W.Material(eps_r=eps_r, sigma=sigma)]
+    p.regions = [W.Region(0, 0.0, L / 2), W.Region(1, L / 2, L)]
+    s = p.sources[0]
+    s.tau, s.t0 = tau, 6 * tau
+    return p
+
+
+def test_dielectric_interface_fresnel():
+    """Normal incidence from vacuum onto eps_r = 4 (n = 2): the reflected
+    field is r = (1 - n)/(1 + n) = -1/3 of the incident one and the
+    transmitted t = 2/(1 + n) = 2/3 (Fresnel; the Yee update with
+    b' = dt/eps of Sec. 3.2).  Envelope peaks within 0.5 %."""
+    p = _two_media(4.0)
+    p.probes = [W.Probe(2048, W.Q_E), W.Probe(6144, W.Q_E)]
+    r = oracle.run(p)
+    a, b = r["records"]
+    split = 4800                                   # incident passes before, the reflection arrives after
+    inc = np.abs(a[:split]).max()
+    ref = np.abs(a[split:]).max()
+    tra = np.abs(b).max()
+    assert ref / inc == pytest.approx(1.0 / 3.0, rel=5e-3)
+    assert tra / inc == pytest.approx(2.0 / 3.0, rel=5e-3)
+    # sign: the reflection is the inverted incident pulse
+    ki, kr = np.argmax(np.abs(a[:split])), split + np.argmax(np.abs(a[split:]))
+    assert np.sign(a[kr]) == -np.sign(a[ki])
+
+
+def test_lossy_dielectric_attenuation():
+    """A lossy dielectric (eps_r = 4, sigma): the field decays as exp(-alpha0 z)
+    with alpha0 = sigma/(2 eps c) (Sec. 2.1, c the speed in the medium); here
+    alpha0 = 1/(2000 dz), so two probes 1,000 cells apart see exp(-1/2).
+    (sigma / (omega eps) = 0.01: the low-loss form is exact to 1e-5.)"""
+    dz = W.DZ_SIT
+    alpha0 = 1.0 / (2000 * dz)
+    n = 2.0
+    sigma = 2.0 * alpha0 * W.EPS0 * n * W.C0
+    p = _two_media(n * n, sigma=sigma, n_steps=12_000)
+    assert p.dz == pytest.approx(dz, rel=1e-12)
+    p.probes = [W.Probe(5000, W.Q_E), W.Probe(6000, W.Q_E)]
+    r = oracle.run(p)
+    a, b = r["records"]
+    assert np.abs(b).max() / np.abs(a).max() == pytest.approx(math.exp(-alpha0 * 1000 * dz), rel=2e-3)
