@@ -384,6 +384,23 @@ def test_pec_reflection_exact():
         assert np.abs(r["records"][k] - ref).max() <= 1e-13 * s.e0
 
 
+def test_hard_source_radiates_both_ways_exact():
+    """A hard source sets E at its cell to S(t) (Sec. 3.1.2); in vacuum at
+    Courant number 1 the Yee scheme carries it unchanged both ways:
+    E_{m_s +- d}^{n+1} = S(t_{n+1-d})."""
+    p = _vacuum()
+    s = p.sources[0]
+    s.kind, s.cell = W.SRC_HARD, 1000
+    cells = [1000, 1001, 1200, 999, 800]
+    p.probes = [W.Probe(c, W.Q_E) for c in cells]
+    r = oracle.run(p)
+    n = np.arange(r["nt"])
+    for k, c in enumerate(cells):
+        a = n + 1 - abs(c - 1000)
+        ref = np.where(a >= 0, s.waveform(a * r["dt"]), 0.0)
+        assert np.abs(r["records"][k] - ref).max() <= 1e-13 * s.e0, c
+
+
 def test_left_going_source_exact():
     p = _vacuum()
     s = p.sources[0]
