@@ -177,6 +177,32 @@ def test_free_evolution_closed_form():
     np.testing.assert_allclose(pd, pd_ref, rtol=0, atol=1e-11 * np.abs(pd_ref).max())
 
 
+def test_grid_probes_of_free_evolution():
+    """The grid solver's density-matrix probes: a medium with an initial
+    coherence, no source and a density too small to radiate (1e6 m^-3)
+    evolves freely, and the records Re rho_10, Im rho_10, Im rho_01, rho_11
+    under index n follow the closed form at (n + 1) dt after rho^{-1/2} =
+    rho_init (the record holds rho^{n+1/2}), to 1e-12."""
+    w21, g1, g2, w0, d = 2e14, 1e12, 3e12, -0.6, 1e-29
+    rho0 = np.array([[0.7, 0.3 + 0.2j], [0.3 - 0.2j, 0.3]])
+    p = W.sit_2lvl(n_cells=256, t_end=0.0, n_steps=2000)
+    p.qms = [W.qm_two_level(1e6, w21, d, g1, g2, w0, rho_init=rho0)]
+    p.sources = []
+    c = 128
+    p.probes = [W.Probe(c, W.Q_RHO_RE, 1, 0), W.Probe(c, W.Q_RHO_IM, 1, 0), W.Probe(c, W.Q_RHO_IM, 0, 1),
+                W.Probe(c, W.Q_RHO_RE, 1, 1), W.Probe(c, W.Q_E)]
+    r = oracle.run(p)
+    t = (np.arange(r["nt"]) + 1) * r["dt"]
+    r10 = rho0[1, 0] * np.exp(-(1j * w21 + g2) * t)
+    wt = w0 + ((rho0[1, 1] - rho0[0, 0]).real - w0) * np.exp(-g1 * t)
+    rec = r["records"]
+    np.testing.assert_allclose(rec[0], r10.real, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(rec[1], r10.imag, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(rec[2], -r10.imag, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(rec[3], (1 + wt) / 2, rtol=0, atol=1e-10)
+    assert np.abs(rec[4]).max() < 1e-6          # the radiated field stays negligible
+
+
 def test_polarisation_current_complex_dipole():
     """d_t P = n3D tr{mu d_t rho} (Sec. 2) for a complex dipole operator and
     non-diagonal H0, with d_t rho from the master equation in matrix-product
