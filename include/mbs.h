@@ -261,7 +261,8 @@ int mbs_device_propagators(mbs_device_t dev, int qm, double dt,
  * path; MBS_E_STATE before the first solve. */
 int mbs_scenario_tile(mbs_scenario_t s, int *tile_steps);
 
-/* The tile plan of the tiled kernels, a pure host query (no device work):
+/* The tile plan of the tiled kernels (the temporal tiles with redundant
+ * halo computation of Sec. 3.2), a pure host query (no device work):
  * whether `tile_steps` steps per launch are valid for tiles of `tile_cells`
  * cells on an `nx`-cell grid with `n_levels` levels, and how many tiles one
  * launch runs.  tile_cells = 512 for N = 2 and 3 (tile_steps a multiple of
@@ -274,7 +275,7 @@ int mbs_scenario_tile(mbs_scenario_t s, int *tile_steps);
  * 2 tile_steps.  MBS_OK with *n_tiles set, or MBS_E_INVALID. */
 int mbs_tile_plan(int n_levels, int tile_cells, int nx, int tile_steps, int *n_tiles);
 
-/* Cells per tile of the last solve's tiled launches (each tile owns
+/* Cells per tile of the last solve's tiled launches (Sec. 3.2; each tile owns
  * tile_cells - 2 tile_steps of them): 512 for N = 2 and 3, 128 or 256 for
  * the tensor-core tiles of N >= 4 (the autotuner may pick either); 0 for the
  * plain path; MBS_E_STATE before the first solve. */
