@@ -317,9 +317,9 @@ int mbs_scenario_counters(mbs_scenario_t s, long long *h2d_bytes, long long *d2h
 int mbs_check_rho_static(const double *rho, int n, int n_levels, double *out, void *cuda_stream);
 
 /* ------------------------------------------------------------------------
- * Driven single cells (Sec. 2.1, the borderline case Nx = 1: the master
- * equation alone, "a solver for the Lindblad equation"; the V-type
- * three-level application example of Sec. 4 is one such system).  A batch of
+ * Driven single cells (Sec. 2.1, the borderline case Nx = 1: with one grid
+ * point the method integrates the Lindblad master equation alone; the
+ * V-type three-level application example of Sec. 4 is one such system).  A batch of
  * n_sys independent systems, each with its own quantum description and its
  * own prescribed field
  *   E^n = e0 envelope(t_n) sin(omega t_n + phase),  t_n = n dt
