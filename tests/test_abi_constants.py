@@ -1,0 +1,50 @@
+"""The binding and the input descriptions restate the header's enumerations
+(statuses, precisions, algorithms, solve flags, source kinds and shapes,
+probe quantities); these must equal the values include/mbs.h declares."""
+import os
+import re
+
+import paper_2005_05412_gb300 as mbs
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_enums():
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "mbs.h")).read(), flags=re.S)
+    vals = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        nxt = 0
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            if "=" in item:
+                name, expr = (x.strip() for x in item.split("=", 1))
+                nxt = eval(expr, {}, dict(vals))
+            else:
+                name = item
+            vals[name] = nxt
+            nxt += 1
+    return vals
+
+
+def test_binding_constants_equal_the_header():
+    h = header_enums()
+    assert h["MBS_OK"] == mbs.MBS_OK and h["MBS_W_NOT_PSD"] == mbs.MBS_W_NOT_PSD
+    for name in ("MBS_E_INVALID", "MBS_E_CUDA", "MBS_E_OOM", "MBS_E_NUMERIC", "MBS_E_TIMEOUT", "MBS_E_STATE"):
+        assert h[name] == getattr(mbs, name), name
+    assert {k: h["MBS_PREC_" + k.upper()] for k in mbs.PREC} == mbs.PREC
+    assert {k: h["MBS_ALGO_" + k.upper()] for k in mbs.ALGO} == mbs.ALGO
+    for name in ("MBS_SOLVE_ONE_AT_A_TIME", "MBS_SOLVE_AUTOTUNE", "MBS_SOLVE_GRAPH", "MBS_SOLVE_WIDE_TILES",
+                 "MBS_SOLVE_TEST_STALL", "MBS_SHAPE_SECH", "MBS_SHAPE_GAUSS"):
+        assert h[name] == getattr(mbs, name), name
+
+
+def test_input_descriptions_equal_the_header():
+    h = header_enums()
+    for w, c in (("SRC_TFSF_RIGHT", "MBS_SRC_TFSF_RIGHT"), ("SRC_TFSF_LEFT", "MBS_SRC_TFSF_LEFT"),
+                 ("SRC_HARD", "MBS_SRC_HARD"), ("Q_E", "MBS_Q_E"), ("Q_H", "MBS_Q_H"),
+                 ("Q_RHO_RE", "MBS_Q_RHO_RE"), ("Q_RHO_IM", "MBS_Q_RHO_IM"),
+                 ("SHAPE_SECH", "MBS_SHAPE_SECH"), ("SHAPE_GAUSS", "MBS_SHAPE_GAUSS")):
+        assert getattr(W, w) == h[c], w
