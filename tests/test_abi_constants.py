@@ -48,3 +48,35 @@ def test_input_descriptions_equal_the_header():
                  ("Q_RHO_RE", "MBS_Q_RHO_RE"), ("Q_RHO_IM", "MBS_Q_RHO_IM"),
                  ("SHAPE_SECH", "MBS_SHAPE_SECH"), ("SHAPE_GAUSS", "MBS_SHAPE_GAUSS")):
         assert getattr(W, w) == h[c], w
+
+
+def header_structs():
+    """name -> [(C type, field)] of every `typedef struct { ... } name;`."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "mbs.h")).read(), flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", text, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"((?:const\s+)?(?:long long|double|int))\s*(\*?)\s*(.*)", decl)
+            base, ptr, names = m.group(1), m.group(2), m.group(3)
+            for nm in names.split(","):
+                nm = nm.strip()
+                star = ptr or nm.startswith("*")
+                fields.append(("ptr" if star else base.replace("const ", ""), nm.lstrip("*").strip()))
+        out[name] = fields
+    return out
+
+
+def test_binding_structures_match_the_header_layouts():
+    import ctypes as C
+    kind = {C.c_int: "int", C.c_double: "double", C.c_longlong: "long long", C.c_void_p: "ptr"}
+    pairs = {"mbs_qm_desc": mbs._QmDesc, "mbs_material": mbs._Material, "mbs_region": mbs._Region,
+             "mbs_bc": mbs._BC, "mbs_source": mbs._Source, "mbs_probe": mbs._Probe, "mbs_opts": mbs._Opts}
+    h = header_structs()
+    assert set(pairs) == set(h)
+    for cname, cls in pairs.items():
+        got = [(kind[t], n) for n, t in cls._fields_]
+        assert got == h[cname], cname
