@@ -106,6 +106,9 @@ def lib():
         L.mbs_scenario_stats.argtypes = [vp, C.POINTER(d), C.POINTER(d), C.POINTER(ll)]
         L.mbs_scenario_counters.argtypes = [vp, C.POINTER(ll), C.POINTER(ll), C.POINTER(ll)]
         L.mbs_scenario_tile.argtypes = [vp, C.POINTER(i)]
+        L.mbs_scenario_tile_cells.argtypes = [vp, C.POINTER(i)]
+        L.mbs_tile_plan.argtypes = [i, i, i, i, C.POINTER(i)]
+        L.mbs_abi_version.argtypes = []
         L.mbs_scenario_set_field.argtypes = [vp, vp, C.c_size_t]
         L.mbs_cells_create.argtypes = [C.POINTER(_QmDesc), i, d, ll, C.POINTER(_Source), i, C.POINTER(vp)]
         L.mbs_cells_solve.argtypes = [vp, i, vp]

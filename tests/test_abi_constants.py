@@ -80,3 +80,43 @@ def test_binding_structures_match_the_header_layouts():
     for cname, cls in pairs.items():
         got = [(kind[t], n) for n, t in cls._fields_]
         assert got == h[cname], cname
+
+
+def test_every_function_declares_its_arguments():
+    """Every prototype of the header has ctypes argtypes of the same kinds
+    (an undeclared argument would be passed as a C int, truncating handles
+    and pointers on 64-bit hosts)."""
+    import ctypes as C
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "mbs.h")).read(), flags=re.S)
+    handles = set(re.findall(r"typedef struct \w+ \*(\w+);", text))
+    structs = set(header_structs())
+    protos = re.findall(r"\n(?:int|void|const char \*)\s*(mbs_\w+)\s*\((.*?)\)\s*;", text, flags=re.S)
+    assert len(protos) == len(mbs.EXPORTS)
+
+    def kind_c(a):
+        a = " ".join(a.split())
+        base = a.replace("const ", "").split()[0]
+        if "*" in a or base in handles:
+            return "ptr"
+        if base in structs:
+            return "struct " + base
+        return {"long": "long long", "size_t": "size_t", "double": "double", "int": "int"}[base]
+
+    py = {C.c_int: "int", C.c_double: "double", C.c_longlong: "long long", C.c_size_t: "size_t",
+          C.c_void_p: "ptr"}
+    structs_py = {mbs._BC: "struct mbs_bc"}
+
+    def kind_py(t):
+        if t in py:
+            return py[t]
+        if t in structs_py:
+            return structs_py[t]
+        assert issubclass(t, C._Pointer), t
+        return "ptr"
+
+    L = mbs.lib()
+    for name, args in protos:
+        want = [] if args.strip() in ("", "void") else [kind_c(a) for a in args.split(",")]
+        got = getattr(L, name).argtypes
+        assert got is not None, name
+        assert [kind_py(t) for t in got] == want, name
