@@ -1,4 +1,5 @@
-"""The float-float field arithmetic of the FP32 kernels, emulated on the CPU.
+"""The float-float field and Kahan state arithmetic of the FP32 kernels,
+emulated on the CPU.
 
 FP32 fields are unevaluated pairs hi + lo of floats.  The update
 f += c (xr - xl) + extra takes the neighbour difference with TwoSum, the
@@ -89,3 +90,25 @@ def test_lazy_float_float_tracks_fp64():
         worst_single = max(worst_single, abs(np.float64(single) - ref) / scale)
     assert worst < 1e-9, worst
     assert worst_single > 1e-7                     # what a single FP32 word would lose
+
+
+def kahan_add(d, c, x):
+    y = f32(x - c)
+    t = f32(d + y)
+    return t, f32(f32(t - d) - y)
+
+
+def test_kahan_keeps_increments_below_half_an_ulp():
+    """A deviation of 0.5 receiving 200,000 increments of 1e-9 (a slow
+    relaxation: each increment is below half an ulp of the value): plain FP32
+    loses every one, the compensated sum (true value d - c) keeps them to
+    1e-6 of their total."""
+    d, c, plain = f32(0.5), f32(0.0), f32(0.5)
+    inc = f32(1e-9)
+    n = 200_000
+    for _ in range(n):
+        d, c = kahan_add(d, c, inc)
+        plain = f32(plain + inc)
+    total = n * np.float64(inc)
+    assert plain == f32(0.5)                                    # stagnation
+    assert abs((np.float64(d) - np.float64(c) - 0.5) - total) <= 1e-6 * total
