@@ -677,3 +677,211 @@ def test_lossy_dielectric_attenuation():
     r = oracle.run(p)
     a, b = r["records"]
     assert np.abs(b).max() / np.abs(a).max() == pytest.approx(math.exp(-alpha0 * 1000 * dz), rel=2e-3)
+
+
+# ------------------------------------------- Courant number below 1
+# At Courant number C < 1 the Yee scheme is no longer exact in vacuum: a
+# wave of angular frequency w travels with the discrete wavenumber k_d of
+#     sin(w dt / 2) = C sin(k_d dz / 2),
+# and both the one-way source and the first-order Mur end differ from their
+# continuous ideals by amounts that follow in closed form from the discrete
+# update equations (Eqs. hupdate/eupdate of Sec. 3.2 in vacuum, written with
+# the normalised field Hh = eta0 H: Hh_f += C (E_f - E_{f-1}), E_m += C
+# (Hh_{m+1} - Hh_m)).  The long workloads run at C = 1 - 2^-13, where none of
+# these effects is visible at C = 1; the pins below fix them at C = 0.5 and at
+# C = 1 - 2^-13 for every frequency of a pulse's band.
+
+def _k_discrete(w, dt, dz, c):
+    return 2.0 / dz * np.arcsin(np.sin(w * dt / 2.0) / c)
+
+
+def _tfsf_amplitudes(w, dt, dz, c):
+    """Plane-wave solution of the discrete grid around a one-way source at
+    cell m_s (total field for m >= m_s, scattered field left of it; Sec.
+    3.1.2 soft source, read as total-field/scattered-field injection of the
+    incident wave E_inc(x, t) = S(t - (x - x_s)/c)).  With z = e^{i w dt},
+    p = e^{i k_d dz}, q = e^{i w dz / 2c} and S = e^{i w t}:
+      total field     E_j^n = A z^n p^-j  (j = m - m_s >= 0),  Hh = -E,
+      scattered field E_j^n = B z^n p^j   (j <= -1),            Hh = +E,
+    the two interface updates -- Hh at face m_s minus C S(t_n), and E at cell
+    m_s plus C S(t_n + dt/2 + dz/2c) -- give two linear equations in A, B."""
+    z = np.exp(1j * w * dt)
+    q = np.exp(1j * w * dz / (2.0 * W.C0))
+    p = np.exp(1j * _k_discrete(w, dt, dz, c) * dz)
+    zh, ph = np.sqrt(z), np.sqrt(p)
+    m = np.zeros(w.shape + (2, 2), complex)
+    rhs = np.zeros(w.shape + (2,), complex)
+    # Hh_0^{n+1/2} - Hh_0^{n-1/2} = C (E_0^n - E_-1^n) - C S(t_n)
+    m[..., 0, 0], m[..., 0, 1], rhs[..., 0] = -c, (zh - 1.0 / zh) / ph + c / p, -c
+    # E_0^{n+1} - E_0^n = C (Hh_1^{n+1/2} - Hh_0^{n+1/2}) + C S(t_n + dt/2 + dz/2c)
+    m[..., 1, 0], m[..., 1, 1], rhs[..., 1] = (z - 1.0) + c * zh / ph, c * zh / ph, c * zh * q
+    x = np.linalg.solve(m, rhs[..., None])[..., 0]
+    return x[..., 0], x[..., 1], p
+
+
+def _mur_reflection(w, dt, dz, c):
+    """First-order Mur end E_0^{n+1} = E_1^n + k (E_1^{n+1} - E_0^n) with
+    k = (C - 1)/(C + 1) (the standard coefficient, reading R6), under the
+    discrete wave E_j^n = z^n (p^j + R p^-j) (j counted from the end cell,
+    p^j arriving): R = p (z + k - p - k z p) / (1 + k z - z p - k p)."""
+    z = np.exp(1j * w * dt)
+    p = np.exp(1j * _k_discrete(w, dt, dz, c) * dz)
+    k = (c - 1.0) / (c + 1.0)
+    return p * (z + k - p - k * z * p) / (1.0 + k * z - z * p - k * p)
+
+
+def _vacuum_line(c, n_cells, n_steps, probes, tau=30e-15, omega=2e14):
+    dz = W.DZ_SIT
+    src = W.Source(W.SRC_TFSF_RIGHT, W.SOURCE_CELL, 1e9, tau, 20 * tau, omega)
+    return W.Problem("vacuum", [], [W.Material()], [W.Region(0, 0.0, n_cells * dz)], n_cells * dz, n_cells,
+                     courant=c, n_steps=n_steps, sources=[src], probes=[W.Probe(m, W.Q_E) for m in probes])
+
+
+@pytest.mark.parametrize("courant", [0.5, W.COURANT_LONG])
+def test_tfsf_and_mur_below_courant_one(courant):
+    """Sec. 3.1.2 sources and Sec. 2.1 boundary at C < 1, frequency by
+    frequency over the band of a 30 fs sech (|S(w)| above 1 % of its peak):
+    (1) the total field 1,000 cells from the source is A p^-1000 S(w): the
+        pulse travels with the discrete k_d, not w/c (the two differ by 0.04
+        rad of phase there at C = 0.5, 4e-6 at C = 1 - 2^-13);
+    (2) the scattered field next to the source is the leak B p^-1 S(w),
+        |B| ~ 3e-6 at C = 0.5 and 1e-9 at C = 1 - 2^-13;
+    (3) the right Mur end returns R(w) of the arriving wave: the difference
+        of a short and a long grid (the long one's end is out of reach) at a
+        probe j cells before the short grid's end is R p^-2j times the
+        arriving wave.
+    An injection time of t_n + dt in the E correction (the C = 1 value) leaks
+    1e-2 (C = 0.5) or 2e-6 (C = 1 - 2^-13) into the scattered field, and a
+    Mur coefficient of the wrong sign reflects 1 (C = 0.5) or 1e-4; both fail."""
+    dz = W.DZ_SIT
+    dt = courant * dz / W.C0
+    tau, m_s, d_tf, j_end = 30e-15, W.SOURCE_CELL, 1000, 1500
+    n_steps = int((40 * tau + (d_tf + 2 * j_end) * dz / W.C0) / dt) + 200
+    short = _vacuum_line(courant, m_s + d_tf + j_end + 1, n_steps, [m_s + d_tf, m_s - 1])
+    long_ = _vacuum_line(courant, m_s + d_tf + int(courant * n_steps) + 200, n_steps, [m_s + d_tf, m_s - 1])
+    rs, rl = oracle.run(short), oracle.run(long_)
+    assert rs["dt"] == pytest.approx(dt, rel=1e-15)
+    nt = rl["nt"]
+    s = long_.sources[0].waveform((np.arange(nt) + 1) * dt)        # record n holds E^{n+1}
+    nf = 4 * nt
+    w = 2 * np.pi * np.fft.rfftfreq(nf, dt)
+    fs = np.fft.rfft(s, nf)
+    band = np.abs(fs) > 1e-2 * np.abs(fs).max()
+    w, fs = w[band], fs[band]
+    a, b, p = _tfsf_amplitudes(w, dt, dz, courant)
+    # (1) total field
+    tf = np.fft.rfft(rl["records"][0], nf)[band] / fs
+    assert np.abs(tf - a * p ** -d_tf).max() < 1e-7
+    cont = np.exp(-1j * w / W.C0 * d_tf * dz)
+    assert np.abs(tf - cont).max() > (1e-2 if courant < 0.9 else 2e-6)   # the discrete k_d is resolved
+    # (2) scattered field
+    sf = np.fft.rfft(rl["records"][1], nf)[band] / fs
+    assert np.abs(sf - b / p).max() < 2e-3 * np.abs(b).max() + 1e-12
+    assert np.abs(rl["records"][1]).max() < 2.0 * np.abs(b).max() * 1e9 + 1e-3   # time domain, V/m
+    # (3) Mur end
+    inc = np.fft.rfft(rl["records"][0], nf)[band]
+    refl = np.fft.rfft(rs["records"][0] - rl["records"][0], nf)[band]
+    r_pred = _mur_reflection(w, dt, dz, courant) * p ** (-2 * j_end)
+    assert np.abs(refl / inc - r_pred).max() < 1e-3 * np.abs(r_pred).max() + 1e-12
+    assert np.abs(r_pred).max() > (1e-4 if courant < 0.9 else 1e-8)       # not trivially zero
+
+
+# ------------------------------------------------- pulse area (Sec. 4.1)
+def _area_slab(area, n_med=300, t2=1e-12):
+    """Two-level slab for the area pins: w21 = 2 pi 2e14 rad/s, d = 1e-29 C m,
+    T1 = T2 = 1 ps, tau = 100 fs sech (w21 tau = 126, so the rotating-wave
+    picture of the area theorem applies), density chosen for a small-signal
+    field attenuation exp(-1) at line centre over the slab; probe 10 cells
+    behind it."""
+    d, w0, tau = 1e-29, 2 * math.pi * 2e14, 100e-15
+    dz = W.DZ_SIT
+    a_per_density = w0 / (2 * W.C0) * d * d * t2 / (W.EPS0 * HBAR)
+    dens = 1.0 / (a_per_density * n_med * dz)
+    qm = W.qm_two_level(dens, w0, d, 1.0 / t2, 1.0 / t2, -1.0)
+    m0, m1 = 52, 52 + n_med
+    nx = m1 + 60
+    mats = [W.Material(), W.Material(qm=0)]
+    regs = [W.Region(0, 0.0, m0 * dz), W.Region(1, m0 * dz, m1 * dz), W.Region(0, m1 * dz, nx * dz)]
+    src = W.Source(W.SRC_TFSF_RIGHT, W.SOURCE_CELL, W.sech_area_amplitude(area, d, tau), tau, 1.2e-12, w0)
+    nt = int((1.2e-12 + 14 * t2 + 0.5e-12) / (W.COURANT_LONG * dz / W.C0))
+    p = W.Problem("area", [qm], mats, regs, nx * dz, nx, courant=W.COURANT_LONG, n_steps=nt,
+                  sources=[src], probes=[W.Probe(m1 + 10, W.Q_E)])
+    return p, dens, d, w0, n_med * dz
+
+
+def _area(e, t, d, w0):
+    """Pulse area (d/hbar) |int envelope dt| = (2 d/hbar) |int E e^{-i w0 t} dt|
+    for E = envelope sin(w0 t + phi) (the envelope's spectrum at the carrier)."""
+    return 2.0 * d / HBAR * abs(np.sum(e * np.exp(-1j * w0 * t)) * (t[1] - t[0]))
+
+
+def test_pulse_area_theorem_long_sech():
+    """Sec. 4.1 (self-induced transparency): a 2 pi sech leaves an absorbing
+    two-level slab with its area, 2 pi within 5 %, while smaller areas are
+    absorbed.  The McCall-Hahn area theorem tan(theta_L / 2) = tan(theta_0 /
+    2) exp(-a L) carries the small-signal attenuation a = Im[(w/c)(sqrt(1 +
+    chi) - 1)] at line centre (the Beer-law pin's chi) to finite area:
+      0.01 pi: exp(-a L) within 2 % (Beer law; the 20-cell wavelength costs ~1 %);
+      0.5 pi:  the area theorem within 5 % (T2 = 10 tau: the theorem holds
+               to a few per cent for a homogeneous line), clearly above the
+               linear Beer value 0.5 pi exp(-a L) (saturation).
+    Tenfold absorption of the first area, or a wrong dipole coupling, fails."""
+    out = {}
+    for area in (0.01 * math.pi, 0.5 * math.pi, 2 * math.pi):
+        p, dens, d, w0, length = _area_slab(area)
+        r = oracle.run(p)
+        t = (np.arange(r["nt"]) + 1) * r["dt"]
+        th_in = _area(p.sources[0].waveform(t), t, d, w0)
+        th_out = _area(r["records"][0], t, d, w0)
+        assert th_in == pytest.approx(area, rel=1e-4)
+        out[area] = (th_in, th_out)
+    g2 = 1e12
+    chi = dens * d * d / (W.EPS0 * HBAR) * (1.0 / (-1j * g2) + 1.0 / (2 * w0 + 1j * g2))   # at w = w21
+    al = np.imag(w0 / W.C0 * (np.sqrt(1 + chi) - 1)) * length
+    assert al == pytest.approx(1.0, rel=1e-3)
+    th_in, th_out = out[0.01 * math.pi]
+    assert th_out / th_in == pytest.approx(math.exp(-al), rel=0.02)
+    th_in, th_out = out[0.5 * math.pi]
+    theorem = 2 * math.atan(math.tan(th_in / 2) * math.exp(-al))
+    assert th_out == pytest.approx(theorem, rel=0.05)
+    assert th_out > 1.15 * th_in * math.exp(-al)
+    th_in, th_out = out[2 * math.pi]
+    assert th_out == pytest.approx(2 * math.pi, rel=0.05)
+
+
+# ------------------------------------------------- per-cell jitter (C1)
+def test_jittered_cells_precess_and_radiate_with_their_factors():
+    """Per-cell factors (density f_n, H0 f_h) of a jittered medium: a cell's
+    coherence evolves as rho_12(0) e^{(i w21 f_h - g2) t} (H0 scaled, the
+    relaxation not), and its first field value E_m^1 = -(dt/eps0) d_tP with
+    d_tP = n3D f_n tr{mu d_t rho^{1/2}} = -2 d n3D f_n Re[(i w21 f_h - g2)
+    rho_12^{1/2}] (mu = -d sigma_x): H^{1/2} = 0 everywhere, so nothing else
+    reaches E^1.  The density is low (1e10 m^-3) so that the field acting
+    back on the cells stays negligible.  Swapping the two factors fails."""
+    w21, g1, g2, d, dens = 2e14, 1e12, 3e12, 1e-29, 1e10
+    rho0 = np.array([[0.7, 0.3 + 0.2j], [0.3 - 0.2j, 0.3]])
+    n = 64
+    p = W.sit_2lvl(n_cells=n, t_end=0.0, n_steps=400)
+    p.qms = [W.qm_two_level(dens, w21, d, g1, g2, -1.0, rho_init=rho0)]
+    p.materials = [W.Material(qm=0)]
+    p.regions = [W.Region(0, 0.0, p.length)]
+    p.sources = []
+    jit = np.ones((n, 2))
+    cells = {20: (1.1, 0.9), 30: (0.85, 1.07), 40: (1.0, 1.0)}
+    for c, (fn, fh) in cells.items():
+        jit[c] = (fn, fh)
+    p.jitter = jit
+    p.probes = []
+    for c in cells:
+        p.probes += [W.Probe(c, W.Q_RHO_RE, 0, 1), W.Probe(c, W.Q_RHO_IM, 0, 1), W.Probe(c, W.Q_E)]
+    r = oracle.run(p)
+    dt = r["dt"]
+    t = (np.arange(r["nt"]) + 1) * dt
+    rec = r["records"]
+    for k, (c, (fn, fh)) in enumerate(cells.items()):
+        lam = 1j * w21 * fh - g2
+        r12 = rho0[0, 1] * np.exp(lam * t)
+        np.testing.assert_allclose(rec[3 * k], r12.real, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(rec[3 * k + 1], r12.imag, rtol=0, atol=1e-12)
+        e1 = -(dt / W.EPS0) * (-2.0 * d * dens * fn * np.real(lam * rho0[0, 1] * np.exp(lam * dt)))
+        assert rec[3 * k + 2][0] == pytest.approx(e1, rel=1e-10)
