@@ -42,6 +42,45 @@ def peaks():
         return {}
 
 
+def compute_peaks():
+    """Arithmetic peaks measured on this GPU model by the library's own
+    microbenchmarks (mbs_peak_rates; profiles/compute_peaks.json, written by
+    `python -m paper_2005_05412_gb300.peaks`), per SM and clock cycle."""
+    try:
+        return json.load(open(os.path.join(ROOT, "profiles", "compute_peaks.json")))
+    except Exception:
+        return {}
+
+
+def issue_peak(cp, sm_mhz, n_sm=152):
+    """Warp instructions per second the SMs can issue at the sampled clock:
+    the measured FP32-FMA warp-instruction rate per SM cycle (the FMA lanes
+    issue one warp instruction per scheduler and cycle), else the nominal 4
+    schedulers x 1 instruction per cycle."""
+    per = cp.get("issue_warp_inst_per_cycle_per_sm")
+    src = "measured (FP32 FMA microbenchmark, profiles/compute_peaks.json) x sampled clock"
+    if not per:
+        per, src = 4.0, "nominal 4 schedulers x 1 warp instruction per cycle x sampled clock"
+    return per * n_sm * sm_mhz / 1e3, src
+
+
+def issue_roof(prof, per_launch_s, clocks, cp, hbm_obj):
+    """The binding roof of the tiled kernels: warp instructions issued per
+    second (ncu smsp__inst_executed.sum per launch of the same kernel and
+    tile shape / the CUDA-event launch time) against the issue peak; the HBM
+    figure by algorithmic bytes (which temporal tiling lets exceed 1) kept as
+    a secondary field."""
+    if not (prof and prof.get("warp_inst") and clocks.get("sm_mhz")):
+        return dict(hbm_obj, note="no current ncu instruction count for this kernel: HBM figure only")
+    ach = prof["warp_inst"] / per_launch_s / 1e9
+    pk, src = issue_peak(cp, clocks["sm_mhz"])
+    return {"bound": "alu", "resource": "instruction issue", "achieved": round(ach, 1), "peak": round(pk, 1),
+            "unit": "Gwarp-inst/s", "frac": round(ach / pk, 4), "traffic": hbm_obj.get("traffic"),
+            "peak_source": src, "warp_inst_per_launch": prof["warp_inst"],
+            "inst_source": "ncu smsp__inst_executed.sum of the same kernel and tile shape (profiles/traffic.json)",
+            "kernel": hbm_obj.get("kernel"), "launch_ms": hbm_obj.get("launch_ms"), "hbm": hbm_obj}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -155,9 +194,11 @@ def time_oracle(p, target_s=12.0, cells=65_536):
     probe = oracle.run(cpu_sample(p, cells, 20))
     rate = cells * 20 / probe["seconds"]
     steps = max(20, int(target_s * rate / cells))
-    r = oracle.run(cpu_sample(p, cells, steps))
+    smp = cpu_sample(p, cells, steps)
+    r = oracle.run(smp)
     return dict(value=cells * steps / r["seconds"] / 1e9, cores=r["threads"], seconds=r["seconds"],
-                sample=f"{cells} medium cells x {steps} steps of the workload (jitter slab, one source)")
+                sample=f"{cells} medium cells x {steps} steps of the workload (jitter slab, one source)",
+                problem=smp, records=r["records"])
 
 
 # ---------------------------------------------------------------- our arm
@@ -226,23 +267,16 @@ def run_ours(args, rank, world, local):
     achieved = alg_bytes * units_per_launch / per_launch_s / 1e9
     prof = load_profile(f"{args.workload}_{args.precision}_T{args.tile}" + ("_C256" if args.wide_tiles else ""))
     traffic = prof.get("dram_bytes") if prof else None
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm or HBM_FALLBACK, "unit": "GB/s",
-            "frac": round(achieved / (hbm or HBM_FALLBACK), 4), "traffic": traffic,
-            "peak_source": "measured" if hbm else "fallback",
-            "binding": "instruction issue (temporal tiles keep the state on chip; see issue)",
-            "kernel": (f"k_tiled_tc<{n_lv}> (tcgen05 3xTF32)" if n_lv >= 4 else
-                       f"k_tiled<{args.precision},N={n_lv}{',percell' if jit else ''}>") + f" T={T}",
-            "alg_bytes_per_cell_step": alg_bytes, "launch_ms": round(per_launch_s * 1e3, 5),
-            "launches_per_solve": launches, "tiled_launches_per_solve": tiled_launches}
+    hbm_obj = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm or HBM_FALLBACK, "unit": "GB/s",
+               "frac": round(achieved / (hbm or HBM_FALLBACK), 4), "traffic": traffic,
+               "peak_source": "measured" if hbm else "fallback",
+               "kernel": (f"k_tiled_tc<{n_lv}> (tcgen05 3xTF32)" if n_lv >= 4 else
+                          f"k_tiled<{args.precision},N={n_lv}{',percell' if jit else ''}>") + f" T={T}",
+               "alg_bytes_per_cell_step": alg_bytes, "launch_ms": round(per_launch_s * 1e3, 5),
+               "launches_per_solve": launches, "tiled_launches_per_solve": tiled_launches}
     clocks = clk.summary()
-    if prof and prof.get("warp_inst") and clocks.get("sm_mhz"):
-        # warp instructions issued per second against the SM's issue limit
-        # (4 schedulers x 1 instruction per clock x 152 SMs at the sampled clock)
-        ach = prof["warp_inst"] / per_launch_s / 1e9
-        pk_i = 4 * 152 * clocks["sm_mhz"] / 1e3
-        roof["issue"] = {"achieved": round(ach, 1), "peak": round(pk_i, 1), "unit": "Gwarp-inst/s",
-                         "frac": round(ach / pk_i, 4), "warp_inst_per_launch": prof["warp_inst"],
-                         "source": "ncu smsp__inst_executed.sum of the same kernel and tile depth"}
+    cp = compute_peaks()
+    roof = issue_roof(prof, per_launch_s, clocks, cp, hbm_obj)
     out = {"metric": METRIC, "value": round(value, 3), "unit": METRIC, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_max * 1e3 / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
@@ -253,20 +287,97 @@ def run_ours(args, rank, world, local):
            "roofline": roof, "clocks": clocks, "gpu_launches": launches * args.steps,
            "wall_s": round(wall, 3)}
     if rank == 0 and not args.quick:
+        # per-result error against the FP64 path (all outside the timed region)
+        par = {}
+        if args.precision == "fp32" and args.nsteps == 0:
+            par[p.name] = fp32_vs_fp64(mbs, stream, torch, p, sc, "tiled", T)
         out["fp64_plain"] = fp64_plain(p, mbs, stream, torch)
         out["six_level"] = level_leg(mbs, stream, torch, "ladder_6lvl", 0, pk, clocks)
         out["three_level"] = level_leg(mbs, stream, torch, "lambda_3lvl", 0, pk, clocks)
+        for leg in ("three_level", "six_level"):
+            par[out[leg]["workload"].split(":")[0]] = out[leg].pop("parity")
         out["cells"] = cells_leg(mbs, stream, torch, clocks)
         out["n_scaling"] = n_scaling_leg(mbs, stream, torch)
         if not args.no_batch:
             out["batch"] = batch_leg(mbs, stream, torch, "fp32")
+            par["batch_mixed"] = out["batch"].pop("parity")
         out["e2e"] = e2e(p, mbs, args, torch, stream)
         if world == 1 and not args.no_cpu:
             cb = time_oracle(p)
             out["cpu_baseline"] = {"value": round(cb["value"], 5), "unit": METRIC, "cores": cb["cores"],
                                    "kind": "oracle", "sample": cb["sample"]}
+            # the GPU paths on the oracle's own timed sample
+            smp = {}
+            for prec, algo in (("fp32", "tiled"), ("fp64", "plain")):
+                g = mbs.run(cb["problem"], precision=prec, algo=algo, stream=stream.cuda_stream)["records"]
+                smp[f"{prec}_{algo}_vs_oracle"] = float(f"{trace_errors(g, cb['records'], cb['problem'].probes)[0]:.3e}")
+            smp["sample"] = cb["sample"]
+            par["cpu_baseline_sample"] = smp
+        par["oracle_windows"] = stored_oracle_parity()
+        out["parity"] = par
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- parity
+def trace_errors(a, b, probes):
+    """Worst relative L2 of the traces a against b over the probes, and the
+    worst for the populations' deviation from their initial value."""
+    worst = dev = 0.0
+    for k, q in enumerate(probes):
+        nb = np.linalg.norm(b[k])
+        if nb == 0.0:
+            continue
+        worst = max(worst, float(np.linalg.norm(a[k] - b[k]) / nb))
+        if q.quantity == W.Q_RHO_RE and np.any(b[k] != b[k][0]):
+            d = b[k] - b[k][0]
+            dev = max(dev, float(np.linalg.norm(a[k] - b[k][0] - d) / np.linalg.norm(d)))
+    return worst, dev
+
+
+def fetch_all(mbs, sc, n):
+    return np.stack([mbs.mbs_fetch_records(sc, k) for k in range(n)])
+
+
+def fp32_vs_fp64(mbs, stream, torch, p, sc32, algo64, tile64=0):
+    """Per-result error of a full-length FP32 solve (the scenario sc32 after
+    its last solve) against the FP64 path on the GPU, every probe trace over
+    the whole run, plus the state checks of both; outside any timed region."""
+    r32 = fetch_all(mbs, sc32, len(p.probes))
+    st32 = mbs.mbs_scenario_stats(sc32)
+    dev = mbs.device_from_problem(p)
+    sc = mbs.scenario_from_problem(dev, p)
+    mbs.mbs_solve([sc], "fp64", algo64, tile_steps=tile64, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    r64 = fetch_all(mbs, sc, len(p.probes))
+    st64 = mbs.mbs_scenario_stats(sc)
+    worst, pdev = trace_errors(r32, r64, p.probes)
+    return {"fp32_vs_fp64_worst_trace": float(f"{worst:.3e}"), "fp32_vs_fp64_worst_population_deviation":
+            float(f"{pdev:.3e}"), "probes": len(p.probes), "steps": p.n_steps, "fp64_path": algo64,
+            "max_trace_dev": float(f"{max(st32['max_trace_dev'], st64['max_trace_dev']):.3e}"),
+            "min_eig": float(f"{min(st32['min_eig'], st64['min_eig']):.3e}")}
+
+
+def stored_oracle_parity():
+    """The oracle comparisons of the GPU test suite (light-cone windows of the
+    full-size workloads, the 2,048-cell SIT case in full, the batch truncated
+    to 5,000 steps), as written by `MBS_PARITY_OUT=profiles/parity_gb300.json
+    python -m pytest tests -m gpu` and committed; summarised by worst case."""
+    f = os.path.join(ROOT, "profiles", "parity_gb300.json")
+    try:
+        d = json.load(open(f))
+    except Exception:
+        return None
+    out = {}
+    for k, v in d.items():
+        if isinstance(v, dict) and "worst" in v:
+            w = v["worst"]
+            out[k] = {"worst_trace": w.get("err"), "worst_population_deviation": max(r.get("dev", 0.0) for r in v["rows"]),
+                      "items": v.get("simulations", len(v["rows"]))}
+        else:
+            out[k] = v
+    out["source"] = "profiles/parity_gb300.json (pytest -m gpu with MBS_PARITY_OUT)"
+    return out
 
 
 # bytes of algorithmic state per cell-step (2 + K values read and written)
@@ -274,7 +385,7 @@ def state_bytes(n_levels, rb=4):
     return 2 * (2 + n_levels * n_levels - 1) * rb
 
 
-def level_leg(mbs, stream, torch, name, T, pk, clocks, reps=2, fp64_steps=1000):
+def level_leg(mbs, stream, torch, name, T, pk, clocks, reps=2, fp64_steps=1000, parity=True):
     """One whole simulation of the multi-level workloads at full size (the
     six-level ladder, 131,072 cells x 50,000 steps, on the tensor-core tiles;
     the three-level Lambda medium, 262,144 cells x 100,000 steps), FP32, with
@@ -313,16 +424,12 @@ def level_leg(mbs, stream, torch, name, T, pk, clocks, reps=2, fp64_steps=1000):
            "tile_choice": "autotuned (MBS_SOLVE_AUTOTUNE)" if T == 0 else "fixed"}
     hb = {"bound": "hbm", "achieved": round(state_bytes(n) * value, 1), "peak": hbm, "unit": "GB/s",
           "frac": round(state_bytes(n) * value / hbm, 4), "alg_bytes_per_cell_step": state_bytes(n),
-          "peak_source": "measured" if pk.get("hbm_gbs") else "fallback", "launch_ms": round(per_launch * 1e3, 5)}
+          "peak_source": "measured" if pk.get("hbm_gbs") else "fallback", "launch_ms": round(per_launch * 1e3, 5),
+          "kernel": (f"k_tiled_tc<{n},{cells // 128}>" if n >= 4 else f"k_tiled<fp32,N={n}>") + f" T={Teff}"}
     prof = load_profile(f"{name}_fp32_T{Teff}" + ("" if n < 4 or cells == 128 else f"_C{cells}"))
     hb["traffic"] = prof.get("dram_bytes") if prof else None
-    if prof and prof.get("warp_inst") and clocks.get("sm_mhz"):
-        ach = prof["warp_inst"] / per_launch / 1e9
-        pk_i = 4 * 152 * clocks["sm_mhz"] / 1e3
-        hb["issue"] = {"achieved": round(ach, 1), "peak": round(pk_i, 1), "unit": "Gwarp-inst/s",
-                       "frac": round(ach / pk_i, 4), "warp_inst_per_launch": prof["warp_inst"],
-                       "source": "ncu smsp__inst_executed.sum of the same kernel and tile depth"}
-    out["roofline"] = hb
+    cp = compute_peaks()
+    out["roofline"] = issue_roof(prof, per_launch, clocks, cp, hb)
     if n >= 4:
         # the propagator apply on the tensor cores: 2 K^2 useful flops per
         # cell-step; the 3xTF32 MMAs execute 3 x 2 x NO x KA per computed cell
@@ -330,15 +437,22 @@ def level_leg(mbs, stream, torch, name, T, pk, clocks, reps=2, fp64_steps=1000):
         ka = (K + 1 + 7) // 8 * 8
         no = (K + sh + 1 + 15) // 16 * 16
         own = cells - 2 * Teff
-        bf16 = pk.get("bf16_tflops")
-        tf32 = bf16 * 1.1 / 2.25 if bf16 else 1900.0 * 1.1 / 2.25
+        mhz = clocks.get("sm_mhz") or 2070.0
+        tfm = cp.get("tf32_mma", {}).get("flops_per_cycle_per_sm")
+        if tfm:
+            tf32 = tfm * 152 * mhz * 1e6 / 1e12
+            src = "measured (tcgen05 kind::tf32 microbenchmark, profiles/compute_peaks.json) x sampled clock"
+        else:
+            bf16 = pk.get("bf16_tflops")
+            tf32 = (bf16 or 1900.0) * 1.1 / 2.25
+            src = "bf16 x nominal tf32/bf16 (1.1/2.25)"
         exec_tf = 3 * 2 * no * ka * value * 1e9 * cells / own / 1e12
         out["tensor"] = {"bound": "tensor", "achieved": round(exec_tf, 1), "peak": round(tf32, 1),
                          "unit": "TFLOP/s", "frac": round(exec_tf / tf32, 4),
-                         "useful_tflops": round(2 * K * K * value * 1e9 / 1e12, 2),
-                         "peak_source": ("measured bf16 x nominal tf32/bf16 (1.1/2.25)" if bf16
-                                         else "fallback bf16 x nominal tf32/bf16"),
+                         "useful_tflops": round(2 * K * K * value * 1e9 / 1e12, 2), "peak_source": src,
                          "kernel": f"k_tiled_tc<{n},{cells // 128}> (tcgen05 kind::tf32, 3xTF32, M=128 N={no} K={ka})"}
+    if parity:
+        out["parity"] = fp32_vs_fp64(mbs, stream, torch, p, sc, "plain")
     q = p.replace(n_steps=fp64_steps)
     dq = mbs.device_from_problem(q)
     sq = mbs.scenario_from_problem(dq, q)
@@ -410,13 +524,19 @@ def cells_leg(mbs, stream, torch, clocks, n_sys=131_072, n_steps=10_000, every=1
     K = 8
     flops = 2 * K * K + 6 * 3 + 4 * K           # propagator apply, rotations, compensated adds
     mhz = clocks.get("sm_mhz") or 2070.0
-    peak = 2 * 128 * 152 * mhz / 1e6             # FP32 FMA lanes x 2 flops x SMs x clock [TFLOP/s]
+    fma = compute_peaks().get("fp32_fma", {}).get("flops_per_cycle_per_sm")
+    if fma:
+        peak = fma * 152 * mhz / 1e6
+        psrc = "measured (FP32 FMA microbenchmark, profiles/compute_peaks.json) x sampled clock"
+    else:
+        peak = 2 * 128 * 152 * mhz / 1e6         # FP32 FMA lanes x 2 flops x SMs x clock [TFLOP/s]
+        psrc = "nominal FP32 FMA rate of 152 SMs x 128 lanes at the sampled SM clock"
     ach = flops * out["fp32"] * 1e9 / 1e12
     res = {"value": round(out["fp32"], 2), "unit": METRIC, "fp64": round(out["fp64"], 2),
            "workload": f"song_vtype: {n_sys} driven three-level systems x {n_steps} steps (Nx = 1)",
            "roofline": {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
                         "frac": round(ach / peak, 4), "alg_flops_per_cell_step": flops,
-                        "peak_source": "FP32 FMA rate of 152 SMs x 128 lanes at the sampled SM clock"}}
+                        "peak_source": psrc}}
     try:
         import oracle
         import time as _t
@@ -460,7 +580,7 @@ def batch_leg(mbs, stream, torch, precision):
     # FP64 and FP32 batched on the first 64 simulations (a bounded sample)
     sub, sub_ps = scs[:64], ps[:64]
     sub_cs = sum(p.n_cells * p.n_steps for p in sub_ps)
-    rate = {}
+    rate, recs = {}, {}
     for prec in ("fp64", "fp32"):
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -469,6 +589,12 @@ def batch_leg(mbs, stream, torch, precision):
         b.record(stream)
         torch.cuda.synchronize()
         rate[prec] = sub_cs / (a.elapsed_time(b) / 1e3) / 1e9
+        recs[prec] = [fetch_all(mbs, sc, len(q.probes)) for sc, q in zip(sub, sub_ps)]
+    errs = [trace_errors(x, y, q.probes) for x, y, q in zip(recs["fp32"], recs["fp64"], sub_ps)]
+    worst = max(range(len(errs)), key=lambda i: errs[i][0])
+    parity = {"fp32_vs_fp64_worst_trace": float(f"{errs[worst][0]:.3e}"), "worst_simulation": worst,
+              "fp32_vs_fp64_worst_population_deviation": float(f"{max(e[1] for e in errs):.3e}"),
+              "simulations": len(sub_ps), "sample": "first 64 simulations, full length, batched FP32 vs batched FP64"}
     n2 = sum(1 for p in ps if p.qms[0].n_levels == 2)
     return {"value": round(batched, 2), "one_at_a_time": round(one, 2), "speedup": round(batched / one, 2),
             "fp64_batched": {"value": round(rate["fp64"], 2), "fp32_same_sample": round(rate["fp32"], 2),
@@ -476,7 +602,8 @@ def batch_leg(mbs, stream, torch, precision):
             "unit": METRIC,
             "workload": f"{len(ps)} simulations ({n2} two-level, {len(ps) - n2} three-level), "
                         f"{cell_steps:.3e} cell-steps", "precision": precision,
-            "tile_steps": {f"N={n}": t for n, t in tiles}, "launch": "CUDA graph replay (MBS_SOLVE_GRAPH)"}
+            "tile_steps": {f"N={n}": t for n, t in tiles}, "launch": "CUDA graph replay (MBS_SOLVE_GRAPH)",
+            "parity": parity}
 
 
 def fp64_plain(p, mbs, stream, torch, steps=4000):

@@ -199,14 +199,26 @@ typedef struct {
                           [1, 26] (256-cell tiles; other depths are checked against the grid).
                           0 = the library's choice: measured with MBS_SOLVE_AUTOTUNE (for N >= 4
                           also the tile width), else 24 (N = 2), 32 (N = 3), 8 / 20 (N >= 4) */
-    int check_every;   /* steps between device-side state checks, 0 = only at the end */
+    int check_every;   /* steps between the periodic state checks (Sec. 2.2: the splitting keeps rho a
+                          density matrix), 0 = only at the end.  Each check samples the smallest
+                          eigenvalue of <= 4096 cells plus the probe cells, and sweeps every cell for
+                          non-finite values and for a negative population or 2 x 2 principal minor of
+                          the stored state (dipole eigenbasis, tolerance 1e-6); in FP32 the sweep
+                          also folds each compensated (Kahan) pair into the canonical pair of its
+                          value, in FP64.  A failed check makes every later step launch of the
+                          scenario return at once.  A single scenario's solve reads the status at
+                          each check and stops there (MBS_E_NUMERIC, the step count in
+                          mbs_scenario_stats); a batch reads it when all members have finished, the
+                          failing member having stopped at its check (tile rounds are the
+                          boundaries: a check runs after the round that crosses a multiple of
+                          check_every).  Records of the steps after a failed check are not written. */
     int flags;         /* MBS_SOLVE_* */
 } mbs_opts;
 
 /* Run every scenario from its initial condition to its last step (previous
  * results are discarded).  `cuda_stream` is a cudaStream_t or NULL for the
  * legacy default stream.  The call returns after the work has completed.
- * Several scenarios on the tiled path (algo AUTO or TILED, check_every 0, no
+ * Several scenarios on the tiled path (algo AUTO or TILED, no
  * MBS_SOLVE_ONE_AT_A_TIME) advance together, grouped by kernel variant (level
  * count and parameter layout): each round of a group's tile_steps steps is
  * one launch over the blocks of the group's scenarios still running
@@ -293,28 +305,50 @@ int mbs_scenario_counters(mbs_scenario_t s, long long *h2d_bytes, long long *d2h
 
 /* Density-matrix check that allocates no device memory.  It has no
  * counterpart in the paper: it exists for callers that cannot call
- * cudaMalloc -- code that runs while a CUDA graph is being captured, or
- * inside a framework that owns every device allocation -- and still want the
+ * cudaMalloc -- a framework that owns every device allocation through its
+ * own pool, or a loop that must not stall on the device-wide
+ * synchronisation an allocation can imply -- and still want the
  * positivity/trace check that mbs_solve applies to its own state.
  *   rho       device pointer, n matrices of n_levels x n_levels complex
  *             (interleaved re, im, row-major), read only
  *   n         1 .. MBS_STATIC_CHECK_MAX (larger n: MBS_E_INVALID, no work)
  *   n_levels  2 .. 6
  *   out       device pointer to 3 doubles, written: smallest eigenvalue of
- *             the Hermitian parts of the finite matrices, largest
- *             |tr rho - 1|, number of matrices with non-finite entries
+ *             the Hermitian parts of the finite matrices (NaN when no matrix
+ *             is finite), largest |tr rho - 1| over the finite matrices (0
+ *             when there is none), number of matrices with a non-finite
+ *             entry
  *   cuda_stream  cudaStream_t or NULL; the call only enqueues work on it
  *             (asynchronous with respect to the host).
  * Scratch: a fixed static device array of 3 doubles per matrix for
- * MBS_STATIC_CHECK_MAX matrices (about 1.5 MB), held by every GPU that loads
- * the library until the process exits.  No cudaMalloc, cudaFree or other
+ * MBS_STATIC_CHECK_MAX matrices (1.5 MB), held by every GPU that loads the
+ * library until the process exits.  No cudaMalloc, cudaFree or other
  * allocating call is made.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  Every call shares the array and it
- * keeps the last call's contents; each call overwrites the entries it reads,
- * so nothing needs clearing, but calls that overlap on the GPU (on different
+ * device address (cudaGetSymbolAddress) with that device current and caches
+ * it for the process; make that first call before any stream capture, and
+ * do not call the entry point on a device after cudaDeviceReset (the cached
+ * address does not survive it).  Every call shares the array and it keeps
+ * the last call's contents; each call writes the n entries it then reads, so
+ * nothing needs clearing, but calls that overlap on the GPU (on different
  * streams, or from several host threads) race on it. */
 int mbs_check_rho_static(const double *rho, int n, int n_levels, double *out, void *cuda_stream);
+
+/* Arithmetic peak of the current GPU, measured by a small kernel, for the
+ * rooflines of the kernels above (the paper has no counterpart).
+ *   which  0: FP32 fused multiply-add (8 independent chains per thread, 8
+ *             blocks of 256 threads per SM); the FP32 lanes also set the
+ *             instruction-issue limit, one warp instruction per scheduler and
+ *             clock, so rate / 64 is the issue peak in warp instructions/s;
+ *          1: FP64 fused multiply-add (the same shape);
+ *          2: TF32 tensor-core MMA, tcgen05.mma kind::tf32 with M = 128,
+ *             N = 256, K = 8 from shared memory into TMEM, issued back to back
+ *             by one thread of one block per SM (every wait bounded: a wait
+ *             that gives up returns MBS_E_TIMEOUT).
+ *   rate     out: flop/s of the last of three launches (the first two warm up)
+ *   seconds  out (or NULL): that launch's duration
+ *   cuda_stream  cudaStream_t or NULL; the call synchronises on its events.
+ * Allocates and frees a small device buffer. */
+int mbs_peak_rates(int which, double *rate, double *seconds, void *cuda_stream);
 
 /* ------------------------------------------------------------------------
  * Driven single cells (Sec. 2.1, the borderline case Nx = 1: with one grid

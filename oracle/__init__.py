@@ -220,3 +220,23 @@ def run(problem, n_threads: int = 0, check_invariants: bool = False):
     if check_invariants:
         out["stats"] = tuple(stats)
     return out
+
+
+def _run_one(args):
+    problem, n_threads = args
+    r = run(problem, n_threads=n_threads)
+    return r["records"], r["dt"], r["nt"]
+
+
+def run_many(problems, processes: int = 0):
+    """Run independent problems on a pool of single-threaded worker
+    processes (started with `spawn`, so that a CUDA context in the caller is
+    never forked).  Returns [(records, dt, nt), ...] in order."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    if processes <= 0:
+        processes = max(1, os.cpu_count() or 1)
+    build()
+    # a worker that dies raises BrokenProcessPool here instead of hanging
+    with ProcessPoolExecutor(processes, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_run_one, [(p, 1) for p in problems]))

@@ -83,7 +83,7 @@ EXPORTS = ["mbs_device_create", "mbs_device_destroy", "mbs_device_propagators", 
            "mbs_scenario_destroy", "mbs_scenario_info", "mbs_scenario_stats", "mbs_scenario_counters", "mbs_solve",
            "mbs_fetch_records", "mbs_last_error", "mbs_abi_version", "mbs_check_rho_static", "mbs_scenario_tile", "mbs_scenario_tile_cells", "mbs_tile_plan",
            "mbs_cells_create", "mbs_cells_solve", "mbs_cells_fetch", "mbs_cells_stats", "mbs_cells_destroy",
-           "mbs_scenario_set_field"]
+           "mbs_scenario_set_field", "mbs_peak_rates"]
 
 
 def lib():
@@ -123,6 +123,8 @@ def lib():
         L.mbs_abi_version.restype = i
         L.mbs_check_rho_static.argtypes = [vp, i, i, vp, vp]
         L.mbs_check_rho_static.restype = i
+        L.mbs_peak_rates.argtypes = [i, C.POINTER(d), C.POINTER(d), vp]
+        L.mbs_peak_rates.restype = i
         for f in ["mbs_device_create", "mbs_device_propagators", "mbs_scenario", "mbs_scenario_info", "mbs_scenario_counters",
                   "mbs_scenario_stats", "mbs_solve", "mbs_fetch_records"]:
             getattr(L, f).restype = i
@@ -324,6 +326,14 @@ def mbs_check_rho_static(rho_ptr: int, n: int, n_levels: int, out_ptr: int, stre
     return _check(lib().mbs_check_rho_static(C.c_void_p(int(rho_ptr)), int(n), int(n_levels),
                                              C.c_void_p(int(out_ptr)),
                                              None if stream is None else C.c_void_p(int(stream))))
+
+
+def mbs_peak_rates(which: int, stream=None):
+    """Measured arithmetic peak of the current GPU: which = 0 FP32 FMA,
+    1 FP64 FMA, 2 TF32 tensor-core MMA.  Returns (flop/s, seconds)."""
+    r, t = C.c_double(), C.c_double()
+    _check(lib().mbs_peak_rates(int(which), C.byref(r), C.byref(t), None if stream is None else C.c_void_p(int(stream))))
+    return r.value, t.value
 
 
 def mbs_abi_version() -> int:

@@ -540,7 +540,7 @@ __global__ void k_plain_a(const Args a, long long n, int cur) {
   constexpr int K = N * N - 1;
   constexpr bool FF = sizeof(real) == 4;
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= a.nx) return;
+  if (m >= a.nx || *a.flags != 0) return;   // (a failed state check stops the solve)
   const int idx = a.off + m;
   const real *E = reinterpret_cast<const real *>(a.E[cur]);
   const real *El = reinterpret_cast<const real *>(a.El[cur]);
@@ -628,7 +628,7 @@ template <typename real>
 __global__ void k_plain_b(const Args a, long long n, int cur) {
   constexpr bool FF = sizeof(real) == 4;
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= a.nx) return;
+  if (m >= a.nx || *a.flags != 0) return;   // (a failed state check stops the solve)
   const int idx = a.off + m;
   const real *E = reinterpret_cast<const real *>(a.E[cur]);
   const real *Elo = reinterpret_cast<const real *>(a.El[cur]);
@@ -773,6 +773,7 @@ static __device__ __noinline__ void rho_probes_lane(const int *s_plc, const int 
 template <typename real, int N, int R, bool KAHAN, int PM>
 __device__ __forceinline__ void tile_body(const Args &a, const int tile, long long n0, int nsteps, int T, int cur,
                                           unsigned char *smem_raw) {
+  if (*a.flags != 0) return;   // a state check failed: the solve stops (the whole block leaves together)
   constexpr int K = N * N - 1;
   constexpr bool FF = sizeof(real) == 4;
   constexpr bool PERCELL = PM == 1;
@@ -1342,9 +1343,104 @@ __global__ void k_check(const Args a, int cur, const int *cells, int n_cells, do
   if (!finite || !isfinite(mn)) {
     atomicOr(a.flags, 1);
     mn = -1e300;
+  } else if (mn < -EIG_TOL) {
+    atomicOr(a.flags, 2);
   }
   min_eig[k] = mn;
   tr_dev[k] = fabs(tr - 1.0);
+}
+
+// ========================================================= periodic sweep
+// One cell of the periodic sweep.  The splitting of Sec. 2.2 keeps rho a
+// density matrix, and so is the stored state x = exp(L0 dt/2) rho: a
+// non-finite field or state value sets flags[0] bit 0; a population of x or
+// a 2 x 2 principal minor x_jj x_kk - |x_jk|^2 (dipole eigenbasis) below
+// -tol sets bit 1 (necessary conditions for positivity, cheap enough for
+// every cell; the sampled check above bisects the smallest eigenvalue).  In
+// FP32 the compensated pair (delta, c) of each component, whose value is
+// delta - c, is folded in FP64 into the canonical pair (round(v), round(v) -
+// v rounded) of that value.
+template <typename real, int N>
+__device__ __forceinline__ void sweep_cell(const Args &a, int m, int dcur, int ecur, int hcur, double tol) {
+  constexpr int K = N * N - 1, NP = N - 1;
+  const int idx = a.off + m;
+  bool finite = isfinite((double)reinterpret_cast<const real *>(a.E[ecur])[idx]) &&
+                isfinite((double)reinterpret_cast<const real *>(a.H[hcur])[idx]);
+  if (a.prec == 1)
+    finite = finite && isfinite((double)reinterpret_cast<const real *>(a.El[ecur])[idx]) &&
+             isfinite((double)reinterpret_cast<const real *>(a.Hl[hcur])[idx]);
+  const int slot = a.qslot[a.mat[idx]];
+  if (slot >= 0) {
+    real *D = reinterpret_cast<real *>(a.D[dcur]);
+    real *Cc = reinterpret_cast<real *>(a.C[dcur]);
+    const double *z = a.zref + (size_t)slot * N * N;
+    double y[N * N];
+    double popsum = 0.0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const size_t at = (size_t)i * a.ld + idx;
+      double v = (double)D[at];
+      if (a.prec == 1) {
+        v -= (double)Cc[at];
+        if (isfinite(v)) {
+          const real hi = (real)v;
+          D[at] = hi;
+          Cc[at] = (real)((double)hi - v);
+        }
+      }
+      finite = finite && isfinite(v);
+      const int fi = i < NP ? i : i + 1;
+      y[fi] = z[fi] + v;
+      if (i < NP) popsum += v;
+    }
+    y[NP] = z[NP] - popsum;
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < N; ++j) ok = ok && y[j] >= -tol;
+    int q = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+      for (int k = j + 1; k < N; ++k, ++q) {
+        const double re = y[N + 2 * q], im = y[N + 2 * q + 1];
+        ok = ok && fma(y[j], y[k], -(re * re + im * im)) >= -tol;
+      }
+    if (finite && !ok) atomicOr(a.flags, 2);
+  }
+  if (!finite) atomicOr(a.flags, 1);
+}
+
+template <typename real, int N>
+__global__ void k_sweep(const Args a, int dcur, int ecur, int hcur, double tol) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < a.nx) sweep_cell<real, N>(a, m, dcur, ecur, hcur, tol);
+}
+
+// block b sweeps the owned cells of tile tasks[b].y of simulation tasks[b].x
+// if that simulation ran the round from step n0
+template <typename real, int N>
+__global__ void k_sweep_batch(const Args *__restrict__ args, const int2 *__restrict__ tasks, int own,
+                              long long n0, int cur, double tol) {
+  const int2 tk = tasks[blockIdx.x];
+  const Args &a = args[tk.x];
+  if (a.nt <= n0) return;
+  const int c0 = tk.y * own, c1 = min(c0 + own, a.nx);
+  for (int m = c0 + (int)threadIdx.x; m < c1; m += blockDim.x) sweep_cell<real, N>(a, m, cur, cur, cur, tol);
+}
+
+template <typename real, int N>
+int sweep_impl(const Args &a, int dcur, int ecur, int hcur, double tol, cudaStream_t st) {
+  const int bs = 256, gs = (a.nx + bs - 1) / bs;
+  k_sweep<real, N><<<gs, bs, 0, st>>>(a, dcur, ecur, hcur, tol);
+  return (int)cudaGetLastError();
+}
+
+template <typename real, int N>
+int sweep_batch_impl(const Args *args, const int2 *tasks, int n_tasks, int own, long long n0, int cur, double tol,
+                     cudaStream_t st) {
+  if (n_tasks <= 0) return 0;
+  k_sweep_batch<real, N><<<n_tasks, 128, 0, st>>>(args, tasks, own, n0, cur, tol);
+  return (int)cudaGetLastError();
 }
 
 template <typename real, int N, bool KAHAN>

@@ -209,9 +209,15 @@ bool eigh_hq(int n, const cd *A, double *w, cd *V) {
   return true;
 }
 
-// exp(A) for a real n x n matrix: scale by 2^-s until ||A||_1 <= 1/4, sum
-// the Taylor series to order 20 (remainder < 1e-32 relative), square s times.
-void expm_taylor(int n, const double *A, double *X) {
+// exp(A) - I for a real n x n matrix, accurate relative to itself: scale by
+// 2^-s until ||A||_1 <= 1/4, sum the Taylor series without its leading
+// identity to order 20 (remainder < 1e-32 relative), and undo the scaling
+// with the squarings in the same form, exp(2B) - I = E (E + 2 I) for
+// E = exp(B) - I.  The step operators act on small deviations through
+// exp(L0 dt) - I, whose entries are ~|L0| dt; forming exp(L0 dt) first and
+// subtracting I would leave them with an absolute error of one ulp of 1 --
+// a systematic error repeated every step.
+void expm1_taylor(int n, const double *A, double *E) {
   double nrm = 0;
   for (int j = 0; j < n; ++j) {
     double s = 0;
@@ -219,7 +225,7 @@ void expm_taylor(int n, const double *A, double *X) {
     nrm = std::max(nrm, s);
   }
   if (!std::isfinite(nrm)) {
-    for (int i = 0; i < n * n; ++i) X[i] = std::nan("");
+    for (int i = 0; i < n * n; ++i) E[i] = std::nan("");
     return;
   }
   int sq = 0;
@@ -228,20 +234,18 @@ void expm_taylor(int n, const double *A, double *X) {
     ++sq;
   }
   const double sc = std::ldexp(1.0, -sq);
-  std::vector<double> B(n * n), term(n * n, 0.0), t2(n * n);
-  for (int i = 0; i < n * n; ++i) B[i] = A[i] * sc;
-  for (int i = 0; i < n * n; ++i) X[i] = 0;
-  for (int i = 0; i < n; ++i) X[i * n + i] = term[i * n + i] = 1.0;
-  for (int k = 1; k <= 20; ++k) {
+  std::vector<double> B(n * n), term(n * n), t2(n * n);
+  for (int i = 0; i < n * n; ++i) B[i] = term[i] = E[i] = A[i] * sc;
+  for (int k = 2; k <= 20; ++k) {
     rmatmul(n, term.data(), B.data(), t2.data());
     for (int i = 0; i < n * n; ++i) {
       term[i] = t2[i] / k;
-      X[i] += term[i];
+      E[i] += term[i];
     }
   }
   for (int k = 0; k < sq; ++k) {
-    rmatmul(n, X, X, t2.data());
-    std::copy(t2.begin(), t2.end(), X);
+    rmatmul(n, E, E, t2.data());
+    for (int i = 0; i < n * n; ++i) E[i] = t2[i] + 2.0 * E[i];
   }
 }
 
@@ -312,29 +316,41 @@ struct QDesc {
 };
 
 struct Step {  // FP64 step operators for one (description, H0 factor)
-  std::vector<double> AK, c, g, Ah;
+  std::vector<double> AK;    // exp(L0 dt) on Bloch deviations
+  std::vector<double> AKm1;  // the same minus I, formed without cancellation
+  std::vector<double> c, g, Ah;
+  std::vector<double> Ehm1;  // exp(L0 dt/2) - I on the full coordinates
   double g0 = 0;
 };
 
 void build_step(const QDesc &q, double hfac, double dt, Step &s) {
   const int N = q.N, N2 = N * N, K = N2 - 1;
-  std::vector<double> M(N2 * N2), Mh(N2 * N2), A(N2 * N2);
+  std::vector<double> M(N2 * N2), Mh(N2 * N2), Eh(N2 * N2), Em1(N2 * N2);
   for (int i = 0; i < N2 * N2; ++i) M[i] = hfac * q.MH[i] + q.MD[i];
   for (int i = 0; i < N2 * N2; ++i) Mh[i] = 0.5 * dt * M[i];
-  s.Ah.assign(N2 * N2, 0.0);
-  expm_taylor(N2, Mh.data(), s.Ah.data());
-  rmatmul(N2, s.Ah.data(), s.Ah.data(), A.data());
+  // exp(L0 dt/2) - I, and exp(L0 dt) - I = Eh (Eh + 2 I)
+  expm1_taylor(N2, Mh.data(), Eh.data());
+  rmatmul(N2, Eh.data(), Eh.data(), Em1.data());
+  for (int i = 0; i < N2 * N2; ++i) Em1[i] += 2.0 * Eh[i];
+  s.Ah = Eh;
+  for (int i = 0; i < N2; ++i) s.Ah[i * N2 + i] += 1.0;
+  s.Ehm1 = Eh;
+  // deviation coordinates drop rho~_{N-1,N-1} = 1 - sum of the others:
+  // (A - I)_ij = Em1[fi][fj] - Em1[fi][N-1] for population columns j
+  s.AKm1.assign(K * K, 0.0);
   s.AK.assign(K * K, 0.0);
   for (int i = 0; i < K; ++i)
     for (int j = 0; j < K; ++j) {
       const int fi = full_of(N, i), fj = full_of(N, j);
-      s.AK[i * K + j] = A[fi * N2 + fj] - (j < N - 1 ? A[fi * N2 + N - 1] : 0.0);
+      s.AKm1[i * K + j] = Em1[fi * N2 + fj] - (j < N - 1 ? Em1[fi * N2 + N - 1] : 0.0);
+      s.AK[i * K + j] = s.AKm1[i * K + j] + (i == j ? 1.0 : 0.0);
     }
+  // affine offset at the reference state: (A - I) yref
   std::vector<double> ay(N2, 0.0);
   for (int i = 0; i < N2; ++i)
-    for (int j = 0; j < N2; ++j) ay[i] += A[i * N2 + j] * q.yref[j];
+    for (int j = 0; j < N2; ++j) ay[i] += Em1[i * N2 + j] * q.yref[j];
   s.c.assign(K, 0.0);
-  for (int i = 0; i < K; ++i) s.c[i] = ay[full_of(N, i)] - q.yref[full_of(N, i)];
+  for (int i = 0; i < K; ++i) s.c[i] = ay[full_of(N, i)];
   // d_t P / n3D = tr(mu L0 exp(L0 dt/2) v) = sum_j lambda_j [M Ah y]_j
   std::vector<double> MAh(N2 * N2);
   rmatmul(N2, M.data(), s.Ah.data(), MAh.data());
@@ -707,7 +723,17 @@ int ensure_bundle(mbs_scenario_s *s, int prec) {
   if ((rc = upload(s->qpar, &b.qpar, prec))) return rc;
   if (s->has_pcell && (rc = upload(s->pcell, &b.pcell, prec))) return rc;
   if (s->has_b2 && (rc = upload(s->pcell2, &b.pcell2, prec))) return rc;
-  if ((rc = upload(s->pr_coef, &b.pr_coef, prec))) return rc;
+  if (prec == 1) {
+    // FP32 records of rho probes hold rho_ab - rho_ab(ref) (the constant term
+    // is added in FP64 when the records are fetched), so that a population
+    // near 1 keeps the full FP32 precision of its deviation
+    std::vector<double> co = s->pr_coef;
+    const int K = s->K;
+    for (size_t k = 0; k < s->pr_cell.size(); ++k) co[k * (K + 1) + K] = 0.0;
+    if ((rc = upload(co, &b.pr_coef, prec))) return rc;
+  } else if ((rc = upload(s->pr_coef, &b.pr_coef, prec))) {
+    return rc;
+  }
   if (prec == 1 && !s->tcw.empty() && (rc = upload_raw(s->tcw, &b.tcw))) return rc;
   const size_t nrec = std::max<size_t>(1, s->pr_cell.size()) * (size_t)s->nt;
   if ((e = cudaMalloc(&b.rec, nrec * rb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc records");
@@ -775,6 +801,7 @@ mbs::Args make_args(mbs_scenario_s *s, int prec) {
   a.pr_coef = b.pr_coef;
   a.tcw = b.tcw;
   a.rec = b.rec;
+  a.zref = s->d_zref;
   a.flags = s->d_flags;
   return a;
 }
@@ -970,7 +997,7 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
     const double bp = (dt / (kEps0 * m.eps_r)) / (1 + dt * m.sigma / (2 * kEps0 * m.eps_r));
     const double cpl = bp * m.overlap * q.n3d;
     double *blk = &s->qpar[(size_t)sl * s->qstride];
-    for (int i = 0; i < K * K; ++i) blk[i] = st.AK[i] - (i % (K + 1) == 0 ? 1.0 : 0.0);
+    for (int i = 0; i < K * K; ++i) blk[i] = st.AKm1[i];
     for (int i = 0; i < K; ++i) {
       blk[K * K + i] = st.c[i];
       blk[K * K + K + i] = cpl * st.g[i];
@@ -1001,10 +1028,11 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
   std::vector<double> d0_slot((size_t)std::max(1, s->n_slot) * K, 0.0);
   for (int sl = 0; sl < s->n_slot; ++sl) {
     const QDesc &q = dev->qms[dev->mats[slot_mat[sl]].qm];
+    // x^0 - yref = (exp(L0 dt/2) - I) yinit + (yinit - yref)
     std::vector<double> x0(N2, 0.0);
     for (int i = 0; i < N2; ++i)
-      for (int j = 0; j < N2; ++j) x0[i] += steps[sl].Ah[i * N2 + j] * q.yinit[j];
-    for (int i = 0; i < K; ++i) d0_slot[sl * K + i] = x0[full_of(N, i)] - q.yref[full_of(N, i)];
+      for (int j = 0; j < N2; ++j) x0[i] += steps[sl].Ehm1[i * N2 + j] * q.yinit[j];
+    for (int i = 0; i < K; ++i) d0_slot[sl * K + i] = x0[full_of(N, i)] + (q.yinit[full_of(N, i)] - q.yref[full_of(N, i)]);
   }
   int bad = 0;
 #pragma omp parallel for schedule(dynamic, 256) reduction(+ : bad)
@@ -1024,7 +1052,7 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
     const double bp = (dt / (kEps0 * mm.eps_r)) / (1 + dt * mm.sigma / (2 * kEps0 * mm.eps_r));
     const double cpl = bp * mm.overlap * q.n3d * fd;
     const size_t col = (size_t)off + m;
-    for (int i = 0; i < K * K; ++i) s->pcell[(size_t)i * ld + col] = st.AK[i] - (i % (K + 1) == 0 ? 1.0 : 0.0);
+    for (int i = 0; i < K * K; ++i) s->pcell[(size_t)i * ld + col] = st.AKm1[i];
     for (int i = 0; i < K; ++i) {
       s->pcell[(size_t)(K * K + i) * ld + col] = st.c[i];
       s->pcell[(size_t)(K * K + K + i) * ld + col] = cpl * st.g[i];
@@ -1032,8 +1060,9 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
     s->pcell[(size_t)(K * K + 2 * K) * ld + col] = cpl * st.g0;
     std::vector<double> x0(N2, 0.0);
     for (int i = 0; i < N2; ++i)
-      for (int j = 0; j < N2; ++j) x0[i] += st.Ah[i * N2 + j] * q.yinit[j];
-    for (int i = 0; i < K; ++i) s->Dinit[(size_t)i * ld + col] = x0[full_of(N, i)] - q.yref[full_of(N, i)];
+      for (int j = 0; j < N2; ++j) x0[i] += st.Ehm1[i * N2 + j] * q.yinit[j];
+    for (int i = 0; i < K; ++i)
+      s->Dinit[(size_t)i * ld + col] = x0[full_of(N, i)] + (q.yinit[full_of(N, i)] - q.yref[full_of(N, i)]);
     if (!std::isfinite(st.AK[0])) ++bad;
   }
   if (bad) return fail(MBS_E_NUMERIC, "non-finite per-cell propagator");
@@ -1308,12 +1337,38 @@ static int launch_state_check(mbs_scenario_s *s, const mbs::Args &a, int c, cuda
   return mbs::launch_check(a, c, s->d_chk_cells, nchk, s->d_chk_min, s->d_chk_tr, s->d_zref, nullptr, st);
 }
 
+// The periodic check of Sec. 2.2's density-matrix properties at a step
+// boundary: the sampled eigenvalue check, then the sweep over every cell
+// (finiteness, populations and 2 x 2 minors; the FP32 Kahan fold).  With
+// `wait` the host reads the status at once and returns true if it failed,
+// so that the caller stops issuing launches; either way a failed check makes
+// every later step launch of the scenario return at once.
+static int periodic_check(mbs_scenario_s *s, const mbs::Args &a, int dcur, int ecur, int hcur, cudaStream_t st,
+                          bool wait, bool *failed) {
+  int r = launch_state_check(s, a, dcur, st);
+  if (!r) {
+    ++s->launches;
+    r = mbs::launch_sweep(a, dcur, ecur, hcur, mbs::EIG_TOL, st);
+  }
+  if (r) return cuda_fail((cudaError_t)r, "check launch");
+  *failed = false;
+  if (wait) {
+    int flags[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(flags, s->d_flags, sizeof flags, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "check status");
+    s->d2h_bytes += sizeof flags;
+    *failed = flags[0] != 0 || flags[1] != 0;
+  }
+  return MBS_OK;
+}
+
 // After the stream has drained: read the check results and device flags.
-static int finish_solve(mbs_scenario_s *s, int prec, int cur) {
+static int finish_solve(mbs_scenario_s *s, int prec, int cur, long long steps_run = -1) {
   cudaError_t e;
   s->solved_prec = prec;
   s->last_cur = cur;
-  s->steps_run = s->nt;
+  s->steps_run = steps_run < 0 ? s->nt : steps_run;
   const int nchk = (int)s->chk_cells.size();
   int flags[4] = {0, 0, 0, 0};
   if ((e = cudaMemcpy(flags, s->d_flags, sizeof flags, cudaMemcpyDeviceToHost)) != cudaSuccess)
@@ -1334,7 +1389,8 @@ static int finish_solve(mbs_scenario_s *s, int prec, int cur) {
     s->st_min = 0;
   }
   if (flags[1]) return fail(MBS_E_TIMEOUT, "a bounded wait on the tensor cores gave up");
-  if (flags[0]) return fail(MBS_E_NUMERIC, "non-finite density matrix");
+  if (flags[0] & 1) return fail(MBS_E_NUMERIC, "non-finite state after %lld steps", s->steps_run);
+  if (flags[0]) return fail(MBS_E_NUMERIC, "density matrix not positive semidefinite after %lld steps", s->steps_run);
   if (nchk && s->st_min < -1e-6) return fail(MBS_E_NUMERIC, "density matrix eigenvalue %.3g < -1e-6", s->st_min);
   return MBS_OK;
 }
@@ -1453,6 +1509,8 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
   int T = o.tile_steps > 0 ? o.tile_steps : default_tile_steps(s->N, s->tc_cells);
   const int chk = o.check_every > 0 ? o.check_every : 0;
   int cur = 0;
+  long long done = 0;
+  bool stopped = false;   // a periodic check failed
   if (algo == MBS_ALGO_TILED) {
     if ((rc = tiled_ok(s, prec, T))) return rc;
     if (o.tile_steps <= 0 && (o.flags & MBS_SOLVE_AUTOTUNE)) {
@@ -1461,8 +1519,7 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
       if (s->N >= 4) s->tc_cells = code_cells(code);
       if ((rc = prepare_solve(s, prec, st))) return rc;   // the trials advanced the state
     }
-    long long done = 0;
-    while (done < s->nt) {
+    while (done < s->nt && !stopped) {
       const int ns = (int)std::min<long long>(T, s->nt - done);
       int r = tiled_launch(s, a, done, ns, T, cur, st);
       ++s->launches;
@@ -1470,17 +1527,18 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
       cur ^= 1;
       done += ns;
       if (chk && done < s->nt && (done / chk) != ((done - ns) / chk))
-        if ((r = launch_state_check(s, a, cur, st))) return cuda_fail((cudaError_t)r, "check launch");
+        if ((r = periodic_check(s, a, cur, cur, cur, st, true, &stopped))) return r;
     }
     s->tile_used = T;
   } else {
-    for (long long n = 0; n < s->nt; ++n) {
+    for (long long n = 0; n < s->nt && !stopped; ++n) {
       int r = mbs::launch_plain_step(a, n, cur, st);
       s->launches += 2;
       if (r) return cuda_fail((cudaError_t)r, "plain launch");
       cur ^= 1;
-      if (chk && (n + 1) % chk == 0 && n + 1 < s->nt)
-        if ((r = launch_state_check(s, a, 0, st))) return cuda_fail((cudaError_t)r, "check launch");
+      done = n + 1;
+      if (chk && (n + 1) % chk == 0 && n + 1 < s->nt)   // plain: D, H in buffers 0, E in cur
+        if ((r = periodic_check(s, a, 0, cur, 0, st, true, &stopped))) return r;
     }
     s->tile_used = 0;
   }
@@ -1489,7 +1547,7 @@ static int solve_one(mbs_scenario_s *s, const mbs_opts &o, cudaStream_t st) {
   if ((rc = launch_state_check(s, a, dcur, st))) return cuda_fail((cudaError_t)rc, "check launch");
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "solve");
-  return finish_solve(s, prec, cur);
+  return finish_solve(s, prec, cur, done);
 }
 
 // Batched tiled solve: every round launches, per kernel variant, one grid
@@ -1523,7 +1581,7 @@ static void group_tasks(BatchGroup &g, const std::vector<mbs_scenario_s *> &ss, 
 // the same options.  Destroying a member scenario drops the graph.
 struct BatchGraph {
   std::vector<mbs_scenario_s *> members;
-  int prec = 0, tile = 0, flags = 0;
+  int prec = 0, tile = 0, flags = 0, check_every = 0;
   std::vector<int> Ts;      // tile depth per group
   std::vector<int> sim_T;   // tile depth per member
   cudaGraphExec_t exec = nullptr;
@@ -1555,6 +1613,7 @@ static void drop_graphs_of(mbs_scenario_s *s) {
 
 static int solve_batch(std::vector<mbs_scenario_s *> &ss, const mbs_opts &o, cudaStream_t st) {
   const int prec = o.precision;
+  const int chk = o.check_every > 0 ? o.check_every : 0;
   int rc;
   for (auto *s : ss) {
     if ((rc = prepare_solve(s, prec, st))) return rc;
@@ -1566,7 +1625,8 @@ static int solve_batch(std::vector<mbs_scenario_s *> &ss, const mbs_opts &o, cud
   if (use_graph) {
     std::lock_guard<std::mutex> lk(g_graph_mu);
     for (auto *g : g_graphs)
-      if (g->members == ss && g->prec == prec && g->tile == o.tile_steps && g->flags == o.flags) {
+      if (g->members == ss && g->prec == prec && g->tile == o.tile_steps && g->flags == o.flags &&
+          g->check_every == chk) {
         cudaError_t e = cudaGraphLaunch(g->exec, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "batched graph replay");
@@ -1721,10 +1781,18 @@ static int solve_batch(std::vector<mbs_scenario_s *> &ss, const mbs_opts &o, cud
         const int active = (int)(std::upper_bound(g.task_nt.begin(), g.task_nt.end(), n0,
                                                   [](long long v, long long y) { return v > y; }) -
                                  g.task_nt.begin());
-        const int r =
-            mbs::launch_tiled_batch(prec, g.N, g.pm, d_args, d_tasks[k], active, smem, n0, g.T, cur, gst[k]);
+        int r = mbs::launch_tiled_batch(prec, g.N, g.pm, d_args, d_tasks[k], active, smem, n0, g.T, cur, gst[k]);
         if (r) return cuda_fail((cudaError_t)r, "batched tiled launch");
         cur ^= 1;
+        // periodic check: the sweep over every cell of the simulations that
+        // ran this round (a failure stops that simulation's later rounds on
+        // the device; the status is read when the batch has finished)
+        const long long n1 = n0 + g.T;
+        if (chk && n1 < nt_max && n1 / chk != n0 / chk) {
+          r = mbs::launch_sweep_batch(prec, g.N, d_args, d_tasks[k], active, mbs::tile_own(g.N, g.T), n0, cur,
+                                      mbs::EIG_TOL, gst[k]);
+          if (r) return cuda_fail((cudaError_t)r, "batched sweep launch");
+        }
       }
     }
     for (size_t k = 0; k < n_fork && x == cudaSuccess; ++k) {
@@ -1778,6 +1846,7 @@ static int solve_batch(std::vector<mbs_scenario_s *> &ss, const mbs_opts &o, cud
     graph->prec = prec;
     graph->tile = o.tile_steps;
     graph->flags = o.flags;
+    graph->check_every = chk;
     for (const auto &g : groups) graph->Ts.push_back(g.T);
     graph->sim_T = sim_T;
     graph->d_args = d_args;
@@ -1813,8 +1882,7 @@ int mbs_solve(mbs_scenario_t *batch, int n_scen, const mbs_opts *opts, void *cud
   for (int i = 0; i < n_scen; ++i)
     if (!batch[i]) return fail(MBS_E_INVALID, "scenario %d is NULL", i);
   // several scenarios on the tiled path advance together, unless asked not to
-  bool batched = n_scen > 1 && !(o.flags & MBS_SOLVE_ONE_AT_A_TIME) && o.algo != MBS_ALGO_PLAIN &&
-                 o.check_every == 0;
+  bool batched = n_scen > 1 && !(o.flags & MBS_SOLVE_ONE_AT_A_TIME) && o.algo != MBS_ALGO_PLAIN;
   for (int i = 0; i < n_scen && batched; ++i)
     batched = batch[i]->N <= 3 && default_algo(batch[i], o.precision) == MBS_ALGO_TILED;
   if (batched) {
@@ -1851,7 +1919,9 @@ int mbs_fetch_records(mbs_scenario_t s, int probe, double *out, size_t cap, size
     e = cudaMemcpy(f.data(), (const float *)b.rec + (size_t)probe * n, n * sizeof(float), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "fetch");
     s->d2h_bytes += (long long)(n * sizeof(float));
-    for (size_t i = 0; i < n; ++i) out[i] = scale * (double)f[i];
+    // rho probes: the FP32 record is the deviation from the reference value
+    const double base = s->pr_q[probe] >= MBS_Q_RHO_RE ? s->pr_coef[(size_t)probe * (s->K + 1) + s->K] : 0.0;
+    for (size_t i = 0; i < n; ++i) out[i] = scale * (double)f[i] + base;
   }
   return MBS_OK;
 }
@@ -2085,7 +2155,7 @@ int mbs_cells_create(const mbs_qm_desc *qms, int n_sys, double dt, long long n_s
     Step st;
     build_step(q, 1.0, dt, st);
     auto put = [&](int row, double v) { c->prm[(size_t)row * n_sys + s] = v; };
-    for (int i = 0; i < K * K; ++i) put(i, st.AK[i] - (i % (K + 1) == 0 ? 1.0 : 0.0));
+    for (int i = 0; i < K * K; ++i) put(i, st.AKm1[i]);
     for (int i = 0; i < K; ++i) put(K * K + i, st.c[i]);
     int p = 0;
     for (int j = 0; j < N; ++j)
@@ -2107,8 +2177,9 @@ int mbs_cells_create(const mbs_qm_desc *qms, int n_sys, double dt, long long n_s
     }
     std::vector<double> x0(N2, 0.0);
     for (int i = 0; i < N2; ++i)
-      for (int j = 0; j < N2; ++j) x0[i] += st.Ah[i * N2 + j] * q.yinit[j];
-    for (int i = 0; i < K; ++i) c->Dinit[(size_t)i * n_sys + s] = x0[full_of(N, i)] - q.yref[full_of(N, i)];
+      for (int j = 0; j < N2; ++j) x0[i] += st.Ehm1[i * N2 + j] * q.yinit[j];
+    for (int i = 0; i < K; ++i)
+      c->Dinit[(size_t)i * n_sys + s] = x0[full_of(N, i)] + (q.yinit[full_of(N, i)] - q.yref[full_of(N, i)]);
     std::copy(q.yref.begin(), q.yref.end(), &c->zref[(size_t)s * N2]);
   }
   for (int s = 0; s < n_sys; ++s) {

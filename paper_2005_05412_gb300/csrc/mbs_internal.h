@@ -104,7 +104,10 @@ struct Args {
   const void *pr_coef;         // [n_probe][K+1]: rho probes h_K, h0
   const float *tcw;            // tensor-core tiles: weight table (tc_weight_table) or null
   void *rec;                   // [n_probe][nt]
-  int *flags;                  // [4] device status words: [0] non-finite state, [1] a bounded wait gave up
+  const double *zref;          // [n_slot][N*N] reference states (full real coordinates, FP64)
+  int *flags;                  // [4] device status words: [0] bit 0 a non-finite value, bit 1 a state that
+                               // is not a density matrix (beyond the tolerance); any bit set makes every
+                               // later step launch of the scenario return at once; [1] a bounded wait gave up
   int test_stall;              // test of the failure path: the tensor-core tiles issue no MMA, so their
                                // first bounded wait expires (about 1 s) and the solve reports a timeout
 };
@@ -141,6 +144,17 @@ int launch_tiled_batch(int prec, int N, int pm, const Args *args, const int2 *ta
                        long long n0, int T, int cur, void *stream);
 int launch_check(const Args &a, int cur, const int *cells, int n_cells, double *out_min_eig,
                  double *out_trace_dev, const void *zref_full, const void *V, void *stream);
+// Periodic sweep over every cell (the state of buffers dcur, E of ecur, H of
+// hcur): non-finite values set flags[0] bit 0, a population or 2 x 2
+// principal minor of the stored state below -tol sets bit 1; in FP32 each
+// compensated pair is folded (in FP64) into the canonical pair of its value.
+int launch_sweep(const Args &a, int dcur, int ecur, int hcur, double tol, void *stream);
+// The same over the owned cells of a batch group's running tiles (tasks of
+// the tiled batch, own = cells owned per tile) after the round from step n0.
+int launch_sweep_batch(int prec, int N, const Args *args, const int2 *tasks, int n_tasks, int own, long long n0,
+                       int cur, double tol, void *stream);
+// Smallest density-matrix eigenvalue the state checks accept.
+constexpr double EIG_TOL = 1e-6;
 
 // Tensor-core tiled kernel for N = 4..6 (mbs_tc.cu): FP32 state, one medium
 // parameter slot, no per-cell operators; tiles of `cells` = 128 or 256 cells

@@ -29,6 +29,8 @@ int plain_step_n45(int N, const Args &a, long long n, int cur, cudaStream_t st);
 int check_n45(int N, const Args &a, int cur, const int *cells, int n_cells, double *mn, double *tr, const double *z,
               cudaStream_t st);
 int plain_step_n6(int N, const Args &a, long long n, int cur, cudaStream_t st);
+int sweep_n45(int N, const Args &a, int dcur, int ecur, int hcur, double tol, cudaStream_t st);
+int sweep_n6(int N, const Args &a, int dcur, int ecur, int hcur, double tol, cudaStream_t st);
 int check_n6(int N, const Args &a, int cur, const int *cells, int n_cells, double *mn, double *tr, const double *z,
              cudaStream_t st);
 
@@ -46,6 +48,23 @@ int launch_check(const Args &a, int cur, const int *cells, int n_cells, double *
   if (a.N <= 3) return check_n23(a.N, a, cur, cells, n_cells, out_min_eig, out_trace_dev, z, st);
   if (a.N <= 5) return check_n45(a.N, a, cur, cells, n_cells, out_min_eig, out_trace_dev, z, st);
   return check_n6(a.N, a, cur, cells, n_cells, out_min_eig, out_trace_dev, z, st);
+}
+
+int sweep_n23(int N, const Args &a, int dcur, int ecur, int hcur, double tol, cudaStream_t st) {
+  switch (N) {
+    case 2:
+      return a.prec == 0 ? sweep_impl<double, 2>(a, dcur, ecur, hcur, tol, st) : sweep_impl<float, 2>(a, dcur, ecur, hcur, tol, st);
+    case 3:
+      return a.prec == 0 ? sweep_impl<double, 3>(a, dcur, ecur, hcur, tol, st) : sweep_impl<float, 3>(a, dcur, ecur, hcur, tol, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_sweep(const Args &a, int dcur, int ecur, int hcur, double tol, void *stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (a.N <= 3) return sweep_n23(a.N, a, dcur, ecur, hcur, tol, st);
+  if (a.N <= 5) return sweep_n45(a.N, a, dcur, ecur, hcur, tol, st);
+  return sweep_n6(a.N, a, dcur, ecur, hcur, tol, st);
 }
 
 }  // namespace mbs

@@ -25,4 +25,14 @@ int check_n45(int N, const Args &a, int cur, const int *cells, int n_cells, doub
   return (int)cudaErrorInvalidValue;
 }
 
+int sweep_n45(int N, const Args &a, int dcur, int ecur, int hcur, double tol, cudaStream_t st) {
+  switch (N) {
+    case 4:
+      return a.prec == 0 ? sweep_impl<double, 4>(a, dcur, ecur, hcur, tol, st) : sweep_impl<float, 4>(a, dcur, ecur, hcur, tol, st);
+    case 5:
+      return a.prec == 0 ? sweep_impl<double, 5>(a, dcur, ecur, hcur, tol, st) : sweep_impl<float, 5>(a, dcur, ecur, hcur, tol, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
 }  // namespace mbs

@@ -21,4 +21,12 @@ int check_n6(int N, const Args &a, int cur, const int *cells, int n_cells, doubl
   return (int)cudaErrorInvalidValue;
 }
 
+int sweep_n6(int N, const Args &a, int dcur, int ecur, int hcur, double tol, cudaStream_t st) {
+  switch (N) {
+    case 6:
+      return a.prec == 0 ? sweep_impl<double, 6>(a, dcur, ecur, hcur, tol, st) : sweep_impl<float, 6>(a, dcur, ecur, hcur, tol, st);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
 }  // namespace mbs

@@ -3,13 +3,17 @@
 // Variant of the state-check kernel (k_check): instead of per-cell results
 // in scenario-owned scratch buffers reduced on the host, the per-matrix
 // results live in a fixed file-scope __device__ array and are reduced on
-// the device into the caller's output.  Callers that cannot call cudaMalloc
-// (code running while a CUDA graph is being captured, or inside a framework
-// that owns every device allocation) can therefore use it.
+// the device into the caller's output.  It serves callers that cannot call
+// cudaMalloc: a framework that owns every device allocation through its own
+// pool, or a loop that must not stall on the device-wide synchronisation an
+// allocation can imply.
 //
 // Every GPU that loads this library holds the scratch array until the
-// process exits: 3 doubles per matrix for MBS_STATIC_CHECK_MAX matrices plus
-// one result slot (about 1.5 MB).
+// process exits: 3 doubles per matrix for MBS_STATIC_CHECK_MAX matrices
+// (1.5 MB).  Its device address is looked up once per device, on the first
+// call with that device current, and cached for the life of the process; a
+// cudaDeviceReset invalidates the cached address (do not call the entry point
+// on a device after resetting it).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -43,13 +47,16 @@ __global__ void k_rho_check(const double *rho, int n, double *scratch) {
     }
   for (int a = 0; a < N; ++a) tr += r[2 * (a * N + a)];
   double mn = finite ? mbs::dev::min_eig_bisect<N>(re, im) : 0.0;
-  scratch[3 * i] = mn;
-  scratch[3 * i + 1] = fabs(tr - 1.0);
-  scratch[3 * i + 2] = (finite && isfinite(mn)) ? 0.0 : 1.0;
+  finite = finite && isfinite(mn);
+  scratch[3 * i] = finite ? mn : 0.0;
+  scratch[3 * i + 1] = finite ? fabs(tr - 1.0) : 0.0;
+  scratch[3 * i + 2] = finite ? 0.0 : 1.0;
 }
 
-// one block: out[0] = min eigenvalue, out[1] = max |tr - 1|, out[2] = number
-// of matrices with non-finite entries
+// one block: out[0] = min eigenvalue, out[1] = max |tr - 1| (both over the
+// finite matrices; out[0] = NaN when there is none), out[2] = number of
+// matrices with non-finite entries.  Reads only entries [0, n) of the
+// scratch array, which this call's first kernel has just written.
 __global__ void k_rho_reduce(const double *scratch, int n, double *out) {
   __shared__ double s_min[256], s_tr[256], s_bad[256];
   double mn = 1e300, tr = 0.0, bad = 0.0;
@@ -71,7 +78,7 @@ __global__ void k_rho_reduce(const double *scratch, int n, double *out) {
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    out[0] = s_min[0];
+    out[0] = s_bad[0] < (double)n ? s_min[0] : nan("");
     out[1] = s_tr[0];
     out[2] = s_bad[0];
   }

@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
   const int own = S::M - 2 * T;
   const int c_own = blockIdx.x * own;
   if (c_own >= a.nx) return;   // the whole block leaves together
+  if (*a.flags != 0) return;   // a state check failed: the solve stops (before any TMEM is held)
 
   const uint32_t sA_hi = smem_u32(smem), sA_lo = sA_hi + S::A_BYTES;
   const uint32_t sB_hi = sA_lo + S::A_BYTES, sB_lo = sB_hi + S::B_BYTES;

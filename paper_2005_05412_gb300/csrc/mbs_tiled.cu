@@ -63,4 +63,16 @@ int launch_tiled_batch(int prec, int N, int pm, const Args *args, const int2 *ta
   return (int)cudaErrorInvalidValue;
 }
 
+int launch_sweep_batch(int prec, int N, const Args *args, const int2 *tasks, int n_tasks, int own, long long n0,
+                       int cur, double tol, void *stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (N == 2)
+    return prec == 0 ? sweep_batch_impl<double, 2>(args, tasks, n_tasks, own, n0, cur, tol, st)
+                     : sweep_batch_impl<float, 2>(args, tasks, n_tasks, own, n0, cur, tol, st);
+  if (N == 3)
+    return prec == 0 ? sweep_batch_impl<double, 3>(args, tasks, n_tasks, own, n0, cur, tol, st)
+                     : sweep_batch_impl<float, 3>(args, tasks, n_tasks, own, n0, cur, tol, st);
+  return (int)cudaErrorInvalidValue;
+}
+
 }  // namespace mbs

@@ -42,21 +42,29 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-def test_fullsize_fp32_vs_fp64(full_runs):
+def log_rows(log, name, rows):
+    """rows: dicts with err (trace) and dev (population deviation, 0 if
+    none); the entry keeps the worst trace row and every row."""
+    log(name, {"simulations": len(rows), "worst": max(rows, key=lambda r: r["err"]), "rows": rows})
+
+
+def test_fullsize_fp32_vs_fp64(full_runs, parity_log):
     p, out = full_runs
     a, b = out["fp32"]["records"], out["fp64"]["records"]
     assert a.shape == (len(p.probes), 200_000)
+    rows = []
     for k, pr in enumerate(p.probes):
         e = rel_l2(a[k], b[k])
-        if pr.quantity == W.Q_RHO_RE:
-            e = max(e, rel_l2(a[k] - 1.0, b[k] - 1.0))
-        assert e <= 1e-4, (k, pr, e)
+        ed = rel_l2(a[k] - 1.0, b[k] - 1.0) if pr.quantity == W.Q_RHO_RE else 0.0
+        rows.append({"cell": pr.cell, "quantity": pr.quantity, "err": e, "dev": ed})
+        assert max(e, ed) <= 1e-4, (k, pr, e, ed)
+    log_rows(parity_log, "sit_2lvl_jitter_fp32_vs_fp64_full", rows)
     for prec in ("fp32", "fp64"):
         st = out[prec]["stats"]
         assert st["max_trace_dev"] <= 1e-6 and st["min_eig"] >= -1e-6, (prec, st)
 
 
-def test_fullsize_window_vs_oracle(full_runs):
+def test_fullsize_window_vs_oracle(full_runs, parity_log):
     """Probe traces within the paper-path bounds (1e-10 FP64, 1e-4 FP32 rel-L2).
     The offset-free deviation rho11 - 1 (a stricter measure, since rho11 ~ 1)
     is held to 1e-4 in FP32 and to 1e-8 in FP64: after 52,000 steps of
@@ -77,13 +85,14 @@ def test_fullsize_window_vs_oracle(full_runs):
         for prec, tol, tol_dev in (("fp64", 1e-10, 1e-8), ("fp32", 1e-4, 1e-4)):
             g = out[prec]["records"][kk][:WINDOW_STEPS]
             e = rel_l2(g, r)
-            report.append((prec, q.cell, q.quantity, e))
+            ed = rel_l2(g - 1.0, r - 1.0) if q.quantity == W.Q_RHO_RE else 0.0
+            report.append({"prec": prec, "cell": q.cell, "quantity": q.quantity, "err": e, "dev": ed})
             assert e <= tol, (prec, q, e, report)
-            if q.quantity == W.Q_RHO_RE:
-                ed = rel_l2(g - 1.0, r - 1.0)
-                report.append((prec, q.cell, "dev", ed, float(np.abs(r - 1.0).max())))
-                assert ed <= tol_dev, (prec, q, ed, report)
+            assert ed <= tol_dev, (prec, q, ed, report)
     print(report)
+    for prec in ("fp64", "fp32"):
+        log_rows(parity_log, f"sit_2lvl_jitter_{prec}_window{WINDOW_STEPS}_vs_oracle",
+                 [r for r in report if r["prec"] == prec])
 
 
 # ------------------------------------------------------------------ six levels
@@ -112,21 +121,25 @@ def full_runs6():
     return p, out
 
 
-def test_fullsize6_fp32_tc_vs_fp64(full_runs6):
+def test_fullsize6_fp32_tc_vs_fp64(full_runs6, parity_log):
     p, out = full_runs6
     a, b = out["fp32"]["records"], out["fp64"]["records"]
     assert a.shape == (len(p.probes), 50_000)
+    rows = []
     for k, pr in enumerate(p.probes):
         e = rel_l2(a[k], b[k])
+        ed = 0.0
         if pr.quantity == W.Q_RHO_RE and np.any(b[k] != b[k][0]):
-            e = max(e, rel_l2(a[k] - b[k][0], b[k] - b[k][0]))
-        assert e <= 1e-4, (k, pr, e)
+            ed = rel_l2(a[k] - b[k][0], b[k] - b[k][0])
+        rows.append({"cell": pr.cell, "quantity": pr.quantity, "level": pr.i, "err": e, "dev": ed})
+        assert max(e, ed) <= 1e-4, (k, pr, e, ed)
+    log_rows(parity_log, "ladder_6lvl_fp32_vs_fp64_full", rows)
     for prec in ("fp32", "fp64"):
         st = out[prec]["stats"]
         assert st["max_trace_dev"] <= 1e-6 and st["min_eig"] >= -1e-6, (prec, st)
 
 
-def test_fullsize6_window_vs_oracle(full_runs6):
+def test_fullsize6_window_vs_oracle(full_runs6, parity_log):
     p, out = full_runs6
     win = W.light_cone_window(p, WINDOW6)
     ref = oracle.run(win)
@@ -141,10 +154,100 @@ def test_fullsize6_window_vs_oracle(full_runs6):
         for prec, tol, tol_dev in (("fp64", 1e-10, 1e-8), ("fp32", 1e-4, 1e-4)):
             g = out[prec]["records"][kk][:WINDOW6]
             e = rel_l2(g, r)
-            report.append((prec, q.cell, q.quantity, q.i, e))
+            ed = rel_l2(g - r[0], r - r[0]) if q.quantity == W.Q_RHO_RE and np.any(r != r[0]) else 0.0
+            report.append({"prec": prec, "cell": q.cell, "quantity": q.quantity, "level": q.i, "err": e, "dev": ed})
             assert e <= tol, (prec, q, e, report)
-            if q.quantity == W.Q_RHO_RE and np.any(r != r[0]):
-                ed = rel_l2(g - r[0], r - r[0])
-                report.append((prec, q.cell, "dev", q.i, ed))
-                assert ed <= tol_dev, (prec, q, ed, report)
+            assert ed <= tol_dev, (prec, q, ed, report)
     print(report)
+    for prec in ("fp64", "fp32"):
+        log_rows(parity_log, f"ladder_6lvl_{prec}_window{WINDOW6}_vs_oracle", [r for r in report if r["prec"] == prec])
+
+
+# --------------------------------------------------------------- three levels
+# The Lambda medium at full size (262,144 cells x 100,000 steps) in the launch
+# configuration bench.py times (FP32 tiles of 40 steps, the depth its
+# autotuner picks), against the FP64 plain path over the whole run and against
+# the oracle on the light-cone window of the first 18,000 steps at probes just
+# inside the medium (which starts at cell 13,107; the probe pulse, t0 = 600
+# fs, reaches them from step ~15,600).  The control pulse enters at the right
+# end and never reaches the window.
+#
+# The FP64 floor: the oracle run again with the levels relabelled (2, 0, 1)
+# -- the same physics, every matrix product in another order -- measures how
+# far two correct FP64 computations of these traces lie apart.  Traces are
+# held to 1e-10 (FP64) and 1e-4 (FP32) relative L2; the offset-free deviation
+# rho_11 - 1 of the near-unity ground population to max(1e-10, 10 x that
+# floor) in FP64 and to 1e-4 in FP32.
+WINDOW3 = 18_000
+NEAR3 = (13_120, 13_500, 14_500)
+PERM3 = (2, 0, 1)      # level i of the relabelled problem is level PERM3[i]
+
+
+@pytest.fixture(scope="module")
+def full_runs3():
+    from paper_2005_05412_gb300 import build
+    build.build()
+    p = W.lambda_3lvl()
+    extra = []
+    for c in NEAR3:
+        extra += [W.Probe(c, W.Q_E)] + [W.Probe(c, W.Q_RHO_RE, k, k) for k in range(3)]
+    p = p.replace(probes=p.probes + extra)
+    out = {"fp32": mbs.run(p, precision="fp32", algo="tiled", tile_steps=40),
+           "fp64": mbs.run(p, precision="fp64", algo="plain")}
+    return p, out
+
+
+def test_fullsize3_fp32_vs_fp64(full_runs3, parity_log):
+    p, out = full_runs3
+    a, b = out["fp32"]["records"], out["fp64"]["records"]
+    assert a.shape == (len(p.probes), 100_000)
+    rows = []
+    for k, pr in enumerate(p.probes):
+        e = rel_l2(a[k], b[k])
+        ed = 0.0
+        if pr.quantity == W.Q_RHO_RE and np.any(b[k] != b[k][0]):
+            ed = rel_l2(a[k] - b[k][0], b[k] - b[k][0])
+        rows.append({"cell": pr.cell, "quantity": pr.quantity, "level": pr.i, "err": e, "dev": ed})
+        assert max(e, ed) <= 1e-4, (k, pr, e, ed)
+    log_rows(parity_log, "lambda_3lvl_fp32_vs_fp64_full", rows)
+    for prec in ("fp32", "fp64"):
+        st = out[prec]["stats"]
+        assert st["max_trace_dev"] <= 1e-6 and st["min_eig"] >= -1e-6, (prec, st)
+
+
+def _relabel3(p):
+    P = np.eye(3)[list(PERM3)]
+    q = p.qms[0]
+    q2 = W.QM(3, q.density, P @ q.h0 @ P.T, P @ q.mu @ P.T, P @ q.rho_init @ P.T, q.lindblad_rates,
+              np.array([P @ o @ P.T for o in q.lindblad_ops]))
+    inv = [PERM3.index(k) for k in range(3)]
+    probes = [W.Probe(r.cell, r.quantity, inv[r.i], inv[r.j]) if r.quantity != W.Q_E else r for r in p.probes]
+    return p.replace(qms=[q2], probes=probes)
+
+
+def test_fullsize3_window_vs_oracle(full_runs3, parity_log):
+    p, out = full_runs3
+    win = W.light_cone_window(p, WINDOW3)
+    win = win.replace(probes=[q for q in win.probes if q.cell in NEAR3])
+    ref = oracle.run(win)
+    ref2 = oracle.run(_relabel3(win))
+    assert ref["nt"] == WINDOW3
+    names = [(q.cell, q.quantity, q.i, q.j) for q in p.probes]
+    report = []
+    for k, q in enumerate(win.probes):
+        kk = names.index((q.cell, q.quantity, q.i, q.j))
+        r, r2 = ref["records"][k], ref2["records"][k]
+        floor = rel_l2(r2, r)
+        floor_dev = rel_l2(r2 - r[0], r - r[0]) if q.quantity == W.Q_RHO_RE and np.any(r != r[0]) else 0.0
+        assert floor <= 1e-11, (q, floor)
+        for prec, tol, tol_dev in (("fp64", 1e-10, max(1e-10, 10 * floor_dev)), ("fp32", 1e-4, 1e-4)):
+            g = out[prec]["records"][kk][:WINDOW3]
+            e = rel_l2(g, r)
+            ed = rel_l2(g - r[0], r - r[0]) if q.quantity == W.Q_RHO_RE and np.any(r != r[0]) else 0.0
+            report.append({"prec": prec, "cell": q.cell, "quantity": q.quantity, "level": q.i, "err": e, "dev": ed,
+                           "oracle_floor": floor, "oracle_floor_dev": floor_dev})
+            assert e <= tol, (prec, q, e, report)
+            assert ed <= tol_dev, (prec, q, ed, report)
+    print(report)
+    for prec in ("fp64", "fp32"):
+        log_rows(parity_log, f"lambda_3lvl_{prec}_window{WINDOW3}_vs_oracle", [r for r in report if r["prec"] == prec])

@@ -75,19 +75,24 @@ def ladder_small():
 
 
 @pytest.mark.parametrize("algo", ["plain", "tiled"])
-def test_sit_fp64(algo):
+def test_sit_fp64(algo, parity_log):
     p = sit_small()
     ref = oracle_run("sit", p)
     got = mbs.run(p, precision="fp64", algo=algo)
-    assert_parity(p, got, ref, TOL64, f"sit fp64 {algo}")
+    worst = assert_parity(p, got, ref, TOL64, f"sit fp64 {algo}")
+    parity_log(f"sit_2lvl_fp64_{algo}_vs_oracle_full", {"worst": {"err": worst}, "rows": [{"dev": 0.0}],
+                                                       "simulations": 1})
 
 
-@pytest.mark.parametrize("algo,tile", [("plain", 0), ("tiled", 16), ("tiled", 8), ("tiled", 36)])
-def test_sit_fp32(algo, tile):
+@pytest.mark.parametrize("algo,tile", [("plain", 0), ("tiled", 16), ("tiled", 8), ("tiled", 36), ("tiled", 24)])
+def test_sit_fp32(algo, tile, parity_log):
     p = sit_small()
     ref = oracle_run("sit", p)
     got = mbs.run(p, precision="fp32", algo=algo, tile_steps=tile)
-    assert_parity(p, got, ref, TOL32, f"sit fp32 {algo} T={tile}")
+    worst = assert_parity(p, got, ref, TOL32, f"sit fp32 {algo} T={tile}")
+    if tile in (0, 24):
+        parity_log(f"sit_2lvl_fp32_{algo}_vs_oracle_full", {"worst": {"err": worst}, "rows": [{"dev": 0.0}],
+                                                           "simulations": 1})
     assert got["stats"]["max_trace_dev"] <= 1e-6
     assert got["stats"]["min_eig"] >= -1e-6
 
