@@ -179,12 +179,15 @@ def job_value(cell_steps, steps, world, t_max):
 # ---------------------------------------------------------------- CPU oracle
 def cpu_sample(p, cells, steps):
     """A slab of the workload for timing the oracle: `cells` consecutive
-    medium cells (with their jitter) driven by the same source."""
+    medium cells (with their jitter) driven by the same source; probes (E and
+    rho_11) 500 and 2,000 cells in, which the pulse has passed within the
+    sampled steps."""
     m0 = int(math.ceil(0.05 * p.n_cells))
     jit = None if p.jitter is None else p.jitter[m0:m0 + cells].copy()
     length = cells * p.dz
+    probes = [W.Probe(c, q) for c in (500, 2000) for q in (W.Q_E, W.Q_RHO_RE)]
     return p.replace(n_cells=cells, length=length, regions=[W.Region(1, 0.0, length)], jitter=jit,
-                     n_steps=steps, t_end=0.0, probes=[W.Probe(cells // 2, W.Q_E)],
+                     n_steps=steps, t_end=0.0, probes=probes,
                      sources=[W.Source(W.SRC_TFSF_RIGHT, 2, *[getattr(p.sources[0], k) for k in
                                                                ("e0", "tau", "t0", "omega", "phase")])])
 

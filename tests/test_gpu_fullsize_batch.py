@@ -7,13 +7,17 @@ autotuned tile depths, recorded as a CUDA graph and replayed.
     32 simulations, every probe;
   * all 512 simulations truncated to the steps it takes the left pulse to
     pass 10 cells into the medium (its centre t0 plus 5 tau, plus the travel
-    time: 1,000 to 9,300 steps), batched on the GPU in FP32 and FP64, against
-    the oracle, at probes 10 cells inside each medium (E and every
-    population) and every rule probe the light cone reaches.  The oracle runs
-    each simulation on the cells that can reach those probes in time (a
-    left-edge source moves at most one cell per step, so a cell beyond
-    (steps + p) / 2 cannot send anything back to a probe at p), or on the
-    whole grid when the simulation's right-edge source could reach a probe.
+    time: 500 to 7,800 steps), batched on the GPU in FP32 and FP64, against
+    the oracle, at the probes the whole pulse has passed: 10 cells inside
+    each medium (E and every population) and the rule probes before it.
+    (A probe deeper in sees only the pulse's leading edge by then; its
+    populations stay below 1e-5, where the FP32 form's absolute rounding,
+    ~1e-9 on populations formed from dipole-eigenbasis components of order
+    0.05, is itself 1e-4 of the trace.)  The oracle runs each simulation on
+    the cells that can reach those probes in time (a left-edge source moves
+    at most one cell per step, so a cell beyond (steps + p) / 2 cannot send
+    anything back to a probe at p), or on the whole grid when the
+    simulation's right-edge source could reach a probe.
 
 Bounds per trace (relative L2): FP32 1e-4, FP64 1e-10; populations also as
 the offset-free deviation from their initial value (FP32 1e-4; FP64 1e-8,
@@ -78,19 +82,17 @@ def _with_front_probes(p):
 
 def _oracle_window(p, steps):
     """The oracle's problem for the first `steps` steps of p, and the indices
-    of p's probes it records.  The whole grid when p is short or a probe at
-    the medium front lies in the light cone of a right-edge source; else the
-    cells [0, (steps + pmax) / 2 + 16) with the probes the left source's
-    light cone reaches (pmax the farthest of them), which evolve exactly as
-    in the full grid."""
+    of p's probes it records (those at or before the front probe, 10 cells
+    into the medium).  The whole grid when p is short or the front probe lies
+    in the light cone of a right-edge source; else the cells [0, (steps +
+    pmax) / 2 + 16), pmax the farthest kept probe, which evolve exactly as in
+    the full grid."""
     right = min([s.cell for s in p.sources if s.kind == W.SRC_TFSF_LEFT], default=10 ** 9)
     front = _medium_front(p) + 10
-    if p.n_cells <= steps + 16 or front >= right - steps - 2:
-        win = p.replace(n_steps=steps, t_end=0.0)
-        return win, list(range(len(p.probes)))
-    lim = min(steps, right - steps - 2)
-    idx = [k for k, q in enumerate(p.probes) if q.cell < lim]
+    idx = [k for k, q in enumerate(p.probes) if q.cell <= front]
     kept = [p.probes[k] for k in idx]
+    if p.n_cells <= steps + 16 or front >= right - steps - 2:
+        return p.replace(n_steps=steps, t_end=0.0, probes=kept), idx
     nx = min(p.n_cells, (steps + max(q.cell for q in kept)) // 2 + 16)
     win = p.replace(n_cells=nx, length=nx * p.dz, n_steps=steps, t_end=0.0, probes=kept,
                     sources=[s for s in p.sources if s.cell < nx - 2])
@@ -153,10 +155,14 @@ def test_batch_truncated_vs_oracle(batch, parity_log):
         for s, ((w, idx), (rec, _dt, nt)) in enumerate(zip(wins, ref)):
             assert nt == ps[s].n_steps
             err = dev = 0.0
+            at = None
             for kw, kp in enumerate(idx):
                 e, ed = trace_err(got[prec][s][kp], rec[kw], w.probes[kw])
+                if max(e, ed) >= max(err, dev):
+                    q = w.probes[kw]
+                    at = (q.cell, q.quantity, q.i)
                 err, dev = max(err, e), max(dev, ed)
             rows.append({"sim": s, "levels": ps[s].qms[0].n_levels, "cells": ps[s].n_cells, "steps": nt,
-                         "err": err, "dev": dev, "window_cells": w.n_cells})
+                         "err": err, "dev": dev, "window_cells": w.n_cells, "worst_probe": at})
             assert err <= tol and dev <= tol_dev, (prec, rows[-1])
         _report(parity_log, f"batch_{prec}_pulse_through_front_vs_oracle", rows)
