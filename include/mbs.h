@@ -159,8 +159,9 @@ enum { MBS_PREC_FP64 = 0,      /* FP64 state and arithmetic */
        MBS_PREC_FP32 = 1 };    /* FP32 fields and Bloch deviations with
                                   compensated (Kahan) accumulation */
 enum { MBS_ALGO_AUTO = 0,
-       MBS_ALGO_PLAIN = 1,     /* one thread per cell, two launches per step
-                                  (Algorithm 1 as written) */
+       MBS_ALGO_PLAIN = 1,     /* one thread per cell, two launches per step: H, rho
+                                  and d_t P at n + 1/2, then E at n + 1 (the loop
+                                  order of Sec. 3.2) */
        MBS_ALGO_TILED = 2 };   /* temporal tiles: tile_steps steps per launch
                                   with halo recompute (the redundant-calculation
                                   loop of Sec. 3.2) */
