@@ -18,8 +18,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 SOURCES_CU = ["mbs_tiled.cu", "mbs_tc.cu", "mbs_cells.cu", "mbs_plain.cu", "mbs_plain45.cu", "mbs_plain6.cu",
               "mbs_static.cu", "mbs_peaks.cu"]
-SOURCES_CPP = ["mbs_host.cpp"]
-HEADERS = ["mbs_internal.h", "mbs_device.cuh"]
+SOURCES_CPP = ["mbs_setup.cpp", "mbs_host.cpp", "mbs_solve.cpp", "mbs_batch.cpp", "mbs_cells_host.cpp"]
+HEADERS = ["mbs_internal.h", "mbs_device.cuh", "mbs_host_internal.h"]
 
 
 def _stale(target, deps):
