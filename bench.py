@@ -286,7 +286,11 @@ def run_ours(args, rank, world, local):
            "data": "synthetic (seeded)",
            "config": {"workload": workload_label(p),
                       "precision": args.precision, "algo": "tiled", "tile_steps": T,
-                      "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)"},
+                      "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
+                      "fp64_baseline_samples": "the FP64 legs time rates on samples: main workload plain and tiled "
+                                               "on its first 4,000 steps, the three- and six-level plain paths on "
+                                               "their first 1,000, the FP64 batch on its first 64 simulations; "
+                                               "the FP32-vs-FP64 parity runs them in full, untimed"},
            "roofline": roof, "clocks": clocks, "gpu_launches": launches * args.steps,
            "wall_s": round(wall, 3)}
     if rank == 0 and not args.quick:
