@@ -709,7 +709,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sit_2lvl_jitter")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--tile", type=int, default=24)
+    ap.add_argument("--tile", type=int, default=32)
     ap.add_argument("--quick", action="store_true", help="skip the FP64, e2e and CPU legs")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-simulation batch leg")

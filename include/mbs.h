@@ -199,7 +199,7 @@ typedef struct {
                           lane for N = 2, 2 for N = 3); N >= 4 in [1, 20] (128-cell tiles) or
                           [1, 26] (256-cell tiles; other depths are checked against the grid).
                           0 = the library's choice: measured with MBS_SOLVE_AUTOTUNE (for N >= 4
-                          also the tile width), else 24 (N = 2), 32 (N = 3), 8 / 20 (N >= 4) */
+                          also the tile width), else 32 (N = 2 and 3), 8 / 20 (N >= 4) */
     int check_every;   /* steps between the periodic state checks (Sec. 2.2: the splitting keeps rho a
                           density matrix), 0 = only at the end.  Each check samples the smallest
                           eigenvalue of <= 4096 cells plus the probe cells, and sweeps every cell for

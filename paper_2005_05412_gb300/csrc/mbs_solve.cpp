@@ -82,9 +82,9 @@ int prepare_solve(mbs_scenario_s *s, int prec, cudaStream_t st) {
 }
 
 // Tile depth when the caller leaves it to the library: the fastest measured
-// on GB300 (two levels: 24 steps, three levels: 32, tensor-core tiles: 8 for
+// on GB300 (two and three levels: 32 steps, tensor-core tiles: 8 for
 // 128 cells, 20 for 256 cells).
-int default_tile_steps(int N, int tc_cells) { return N == 2 ? 24 : N == 3 ? 32 : tc_cells == 256 ? 20 : 8; }
+int default_tile_steps(int N, int tc_cells) { return N <= 3 ? 32 : tc_cells == 256 ? 20 : 8; }
 
 // Whether scenario s runs on the tensor-core tiles (N = 4..6 in FP32 with a
 // single medium and no per-cell operators).
