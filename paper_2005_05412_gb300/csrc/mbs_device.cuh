@@ -61,13 +61,29 @@ __device__ __forceinline__ void sincos_m1_taylor(float x, float &s, float &cm1) 
   cm1 = t * pc;
 }
 
-// |x| > 1/2 in the tiles: out of line, so that the common path carries no
-// library code; (sin x, cos x - 1) returned by value, so that the caller's
+// |x| > 1/2 in the tensor-core tiles: out of line, so that the common path
+// carries no library code; (sin x, cos x - 1) returned by value, so that the caller's
 // results stay in registers
 static __device__ __noinline__ float2 sincos_m1_far(float x) {
   float2 r;
   sincos_m1_wide(x, r.x, r.y);
   return r;
+}
+
+// The same polynomials two orders shorter (sin x to x^7, cos x - 1 to
+// x^8), for angles known to satisfy |x| <= 1/2: the alternating series'
+// first omitted terms, x^9/9! <= 5.4e-9 and x^10/10! <= 2.7e-10, stay below
+// half an ulp of sin x and of cos x - 1 on that range.
+__device__ __forceinline__ void sincos_m1_taylor_half(float x, float &s, float &cm1) {
+  const float t = x * x;
+  float ps = fmaf(t, -1.0f / 5040.0f, 1.0f / 120.0f);
+  ps = fmaf(t, ps, -1.0f / 6.0f);
+  ps = fmaf(t, ps, 1.0f);
+  s = x * ps;
+  float pc = fmaf(t, 1.0f / 40320.0f, -1.0f / 720.0f);
+  pc = fmaf(t, pc, 1.0f / 24.0f);
+  pc = fmaf(t, pc, -0.5f);
+  cm1 = t * pc;
 }
 
 // sin x and cos x - 1 for any x
@@ -108,22 +124,16 @@ __device__ __forceinline__ void sincos_m1(double x, double &s, double &cm1) {
 }
 
 // Rotation forms of the Bloch step (FP32; FP64 always takes sincos_m1):
-//   ROT_TAYLOR: every angle of the warp is known to satisfy |x| <= 1/2;
-//   ROT_FAR:    any angle, those beyond 1/2 out of line;
-//   ROT_INLINE: any angle, the library routine inline.
-enum { ROT_TAYLOR = 0, ROT_FAR = 1, ROT_INLINE = 2 };
+//   ROT_TAYLOR: every angle of the warp is known to satisfy |x| <= 1/2
+//               (the shorter polynomials);
+//   ROT_INLINE: any angle, the library routine inline beyond 1/2.
+enum { ROT_TAYLOR = 0, ROT_INLINE = 2 };
 template <int ROT>
 __device__ __forceinline__ void sincos_m1_sel(float x, float &s, float &cm1) {
-  if constexpr (ROT == ROT_INLINE) {
+  if constexpr (ROT == ROT_INLINE)
     sincos_m1(x, s, cm1);
-  } else {
-    sincos_m1_taylor(x, s, cm1);
-    if (ROT == ROT_FAR && fabsf(x) > 0.5f) {
-      const float2 r = sincos_m1_far(x);
-      s = r.x;
-      cm1 = r.y;
-    }
-  }
+  else
+    sincos_m1_taylor_half(x, s, cm1);
 }
 template <int ROT>
 __device__ __forceinline__ void sincos_m1_sel(double x, double &s, double &cm1) {
@@ -400,6 +410,35 @@ __device__ __forceinline__ real bloch_step_b2(const PrmBloch2<real> &q, real e, 
     d[1] += a1;
     d[2] += a2;
   }
+  return pw;
+}
+
+// The structured two-level step with blocked accumulation (FP32 tiles): the
+// deviation is d + acc, where d stays fixed for the whole tile and acc
+// collects the tile's increments; the tile folds acc into d error-free at its
+// end (the stored pair keeps the Kahan form d - c, c = -acc).  An increment
+// rounds against |acc| (at most the tile's T increments) instead of against
+// |d|: 3 additions per step instead of Kahan's 12, at the price of the 3
+// additions that form d + acc.  x is the rotation angle (zero in vacuum
+// cells, whose rows are zero).
+template <int ROT>
+__device__ __forceinline__ float bloch_step_b2_blocked(const PrmBloch2<float> &q, float x, const float (&d)[3],
+                                                       float (&acc)[3], float (&u)[3]) {
+  float s, cm1;
+  sincos_m1_sel<ROT>(x, s, cm1);
+  const float s1 = d[1] + acc[1];
+  const float s2 = d[2] + acc[2];
+  u[0] = d[0] + acc[0];
+  const float xa = q.zr(0) + s1;
+  const float xb = q.zr(1) + s2;
+  const float ra = cm1 * xa - s * xb;
+  const float rb = s * xa + cm1 * xb;
+  u[1] = s1 + ra;
+  u[2] = s2 + rb;
+  const float pw = q.w0c * u[0] + q.w2c * u[2];
+  acc[0] += q.a00 * u[0] + q.a02 * u[2];
+  acc[1] += ra + q.a11 * u[1];
+  acc[2] += rb + q.a20 * u[0] + q.a22 * u[2];
   return pw;
 }
 
@@ -805,6 +844,9 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
   constexpr int K = N * N - 1;
   constexpr bool FF = sizeof(real) == 4;
   constexpr bool PERCELL = PM == 1;
+  // FP32 structured two-level rows: blocked accumulation of the deviation
+  // (bloch_step_b2_blocked); cc holds acc = -c while the tile runs
+  constexpr bool BLK = FF && KAHAN && PM == 2;
   static_assert(PM != 2 || N == 2, "structured rows are two-level");
   // the probes of this tile's owned cells (build_probe_list, keyed by cell),
   // at a fixed offset, so that a probe lane's step reads a short list
@@ -868,6 +910,9 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
     else
 #pragma unroll
       for (int j = 0; j < R; ++j) cc[i][j] = real(0);
+    if constexpr (BLK)
+#pragma unroll
+      for (int j = 0; j < R; ++j) cc[i][j] = -cc[i][j];
   }
   // field coefficients per cell (pad cells outside the grid have zeros)
   real ca[R], cb[R], ch[R], mk[R];
@@ -926,6 +971,11 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
       b2[j].w2c = pc[(size_t)6 * a.ld + base + j];
     }
   }
+  // rotation angle per unit field of each cell (zero in vacuum cells)
+  real kc[BLK ? R : 1];
+  if constexpr (BLK)
+#pragma unroll
+    for (int j = 0; j < R; ++j) kc[j] = mk[j] * b2[j].kap(0);
   // warp-uniform: does the tile touch a source, a boundary cell, a probe?
   const int t_lo = tb + wib * SPAN, t_hi = t_lo + SPAN;   // this warp's cells [t_lo, t_hi)
   bool any_src = false;
@@ -1001,21 +1051,40 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
     real pw[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) pw[j] = real(0);
-    // one instantiation per rotation form (see sincos_m1_sel)
-    auto bloch = [&](auto rot_tag) {
+    // one instantiation per rotation form (see sincos_m1_sel) and per
+    // probe form (PARK: the warp holds a probe cell, whose rotated state is
+    // parked in shared memory; the other warps carry no stores for it)
+    auto bloch = [&](auto rot_tag, auto park_tag) {
       constexpr int ROT = decltype(rot_tag)::value;
-      real ej[R];
+      constexpr bool PARK = decltype(park_tag)::value;
+      real ej[R];   // the field of medium cells (BLK: the rotation angle)
 #pragma unroll
-      for (int j = 0; j < R; ++j) ej[j] = fld_val<real>(E[j], El[j]) * mk[j];
+      for (int j = 0; j < R; ++j) ej[j] = fld_val<real>(E[j], El[j]) * (BLK ? kc[BLK ? j : 0] : mk[j]);
       if constexpr (PM == 0) {
         real u[K][R];
         bloch_step_rows<real, N, R, KAHAN, ROT>(mb, ej, d, cc, u, pw);
 #pragma unroll
         for (int j = 0; j < R; ++j) {
           pw[j] *= mk[j];
-          if (pmask & (1u << j))   // park u of probe cells (predicated stores)
+          if (PARK && (pmask & (1u << j)))   // park u of probe cells (predicated stores)
 #pragma unroll
             for (int i = 0; i < K; ++i) s_u[j * K + i] = u[i][j];
+        }
+      } else if constexpr (BLK) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          float dj[3], aj[3], u[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            dj[i] = d[i][j];
+            aj[i] = cc[i][j];
+          }
+          pw[j] = bloch_step_b2_blocked<ROT>(b2[j], ej[j], dj, aj, u);
+#pragma unroll
+          for (int i = 0; i < 3; ++i) cc[i][j] = aj[i];
+          if (PARK && (pmask & (1u << j)))
+#pragma unroll
+            for (int i = 0; i < 3; ++i) s_u[j * 3 + i] = u[i];
         }
       } else {
 #pragma unroll
@@ -1037,7 +1106,7 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
             d[i][j] = dj[i];
             cc[i][j] = cj[i];
           }
-          if (pmask & (1u << j))   // park u of probe cells (predicated stores)
+          if (PARK && (pmask & (1u << j)))   // park u of probe cells (predicated stores)
 #pragma unroll
             for (int i = 0; i < K; ++i) s_u[j * K + i] = u[i];
         }
@@ -1048,16 +1117,24 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
     // the library path inline at every angle; the three-level tiles run
     // faster with that single form)
     if (warp_med) {
+      using rot_inline = std::integral_constant<int, ROT_INLINE>;
+      using rot_taylor = std::integral_constant<int, ROT_TAYLOR>;
       if constexpr (FF && N == 2) {
-        real e_max = real(0);
+        real e_max = real(0);   // largest |angle| (BLK) or |field| of the lane's medium cells
 #pragma unroll
-        for (int j = 0; j < R; ++j) e_max = fmax(e_max, fabs(fld_val<real>(E[j], El[j]) * mk[j]));
-        if (__any_sync(FULL, e_max * kap_max > real(0.5)))
-          bloch(std::integral_constant<int, ROT_INLINE>{});
-        else
-          bloch(std::integral_constant<int, ROT_TAYLOR>{});
+        for (int j = 0; j < R; ++j)
+          e_max = fmax(e_max, fabs(fld_val<real>(E[j], El[j]) * (BLK ? kc[BLK ? j : 0] : mk[j])));
+        const bool wide = __any_sync(FULL, (BLK ? e_max : e_max * kap_max) > real(0.5));
+        if (any_probe) {
+          if (wide) bloch(rot_inline{}, std::true_type{});
+          else bloch(rot_taylor{}, std::true_type{});
+        } else {
+          if (wide) bloch(rot_inline{}, std::false_type{});
+          else bloch(rot_taylor{}, std::false_type{});
+        }
       } else {
-        bloch(std::integral_constant<int, ROT_INLINE>{});
+        if (any_probe) bloch(rot_inline{}, std::true_type{});
+        else bloch(rot_inline{}, std::false_type{});
       }
     }
     if (warp_med) {
@@ -1192,6 +1269,17 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
       ff_renorm(E[j], El[j]);
       ff_renorm(H[j], Hl[j]);
     }
+  }
+  if constexpr (BLK) {   // d + acc -> the Kahan pair (s, -e) of its exact sum
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        float sm, er;
+        two_sum(d[i][j], cc[i][j], sm, er);
+        d[i][j] = sm;
+        cc[i][j] = -er;
+      }
   }
   real *Eo = reinterpret_cast<real *>(a.E[cur ^ 1]);
   real *Ho = reinterpret_cast<real *>(a.H[cur ^ 1]);

@@ -12,6 +12,10 @@ identities written in sin and cos - 1.  In FP32 with fused multiply-adds
 * the polynomials hold sin x to 2 ulp and cos x - 1 to 3 ulp of the result
   on |x| <= 1/2, and still on |x| <= 1: the guard's threshold keeps a factor
   of 2 in hand (beyond |x| ~ 1.2 the truncated series fails);
+* the two-level tiles' shorter polynomials (sin x to x^7, cos x - 1 to x^8,
+  taken only when a warp vote has shown every |x| <= 1/2) hold the same 2 and
+  3 ulp there (the omitted terms are below half an ulp), and fail beyond
+  |x| ~ 1, which is what the vote is for;
 * the identities reproduce sin and cos - 1 of the difference to 3 x 2^-24
   absolute, the order of rounding the difference angle itself in FP32
   (the rotation's entries are of order 1), and a wrong sign in either
@@ -40,6 +44,19 @@ def taylor(x):
     pc = fma(t, pc, f32(-0.5))
     cm1 = f32(t * pc)
     return s, cm1
+
+
+def taylor_half(x):
+    x = f32(x)
+    t = f32(x * x)
+    ps = fma(t, f32(-1.0 / 5040.0), f32(1.0 / 120.0))
+    ps = fma(t, ps, f32(-1.0 / 6.0))
+    ps = fma(t, ps, f32(1.0))
+    s = f32(x * ps)
+    pc = fma(t, f32(1.0 / 40320.0), f32(-1.0 / 720.0))
+    pc = fma(t, pc, f32(1.0 / 24.0))
+    pc = fma(t, pc, f32(-0.5))
+    return s, f32(t * pc)
 
 
 def ulp(v):
@@ -79,3 +96,20 @@ def test_angle_difference_identities():
         worst_c = max(worst_c, abs(np.float64(mv) - cosm1(d)))
     assert worst_s <= 3 * 2.0 ** -24, worst_s
     assert worst_c <= 3 * 2.0 ** -24, worst_c
+
+
+def test_short_polynomials_on_half_the_range():
+    rng = np.random.default_rng(6)
+    xs = np.concatenate([rng.uniform(-0.5, 0.5, 20_000), np.geomspace(1e-12, 0.5, 2_000),
+                         -np.geomspace(1e-12, 0.5, 2_000), [0.5, -0.5]]).astype(np.float32)
+    es, ec = 0.0, 0.0
+    for x in xs:
+        s, c = taylor_half(x)
+        xd = np.float64(x)
+        es = max(es, abs(np.float64(s) - np.sin(xd)) / ulp(np.sin(xd)))
+        if xd != 0.0:
+            ec = max(ec, abs(np.float64(c) - cosm1(xd)) / ulp(cosm1(xd)))
+    assert es <= 2.0, es
+    assert ec <= 3.0, ec
+    s1, c1 = taylor_half(1.0)   # beyond the vote's range the shorter series fails
+    assert abs(np.float64(s1) - np.sin(1.0)) / ulp(np.sin(1.0)) > 10
