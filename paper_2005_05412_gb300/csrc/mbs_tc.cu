@@ -448,8 +448,10 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
       const float ej = fld_val<float>(E, El) * mk;
       float sn[N], cm[N];   // sin, cos - 1 of theta_0k (k = 0: zero angle)
       sn[0] = cm[0] = 0.0f;
+      // the shorter polynomials, exact to 2 and 3 ulp while |theta_0k| <= 1/2;
+      // larger angles take the library routine below
 #pragma unroll
-      for (int k = 1; k < N; ++k) sincos_m1_taylor(kap0[k - 1] * ej, sn[k], cm[k]);
+      for (int k = 1; k < N; ++k) sincos_m1_taylor_half(kap0[k - 1] * ej, sn[k], cm[k]);
       if (__any_sync(FULL, fabsf(ej) * *s_kmax > 0.5f))   // a strong field somewhere in the warp
         for (int k = 1; k < N; ++k)
           if (fabsf(kap0[k - 1] * ej) > 0.5f) {

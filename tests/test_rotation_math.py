@@ -12,10 +12,11 @@ identities written in sin and cos - 1.  In FP32 with fused multiply-adds
 * the polynomials hold sin x to 2 ulp and cos x - 1 to 3 ulp of the result
   on |x| <= 1/2, and still on |x| <= 1: the guard's threshold keeps a factor
   of 2 in hand (beyond |x| ~ 1.2 the truncated series fails);
-* the two-level tiles' shorter polynomials (sin x to x^7, cos x - 1 to x^8,
-  taken only when a warp vote has shown every |x| <= 1/2) hold the same 2 and
-  3 ulp there (the omitted terms are below half an ulp), and fail beyond
-  |x| ~ 1, which is what the vote is for;
+* the shorter polynomials (sin x to x^7, cos x - 1 to x^8) that the
+  two-level tiles take once a warp vote has shown every |x| <= 1/2, and the
+  tensor-core tiles for every angle within 1/2 (the library routine replaces
+  the others), hold the same 2 and 3 ulp there (the omitted terms are below
+  half an ulp), and fail beyond |x| ~ 1, which is what the guards are for;
 * the identities reproduce sin and cos - 1 of the difference to 3 x 2^-24
   absolute, the order of rounding the difference angle itself in FP32
   (the rotation's entries are of order 1), and a wrong sign in either
@@ -87,8 +88,8 @@ def test_angle_difference_identities():
     worst_s, worst_c = 0.0, 0.0
     for _ in range(5_000):
         a, b = rng.uniform(-0.5, 0.5, 2).astype(np.float32)   # theta_0k, theta_0j
-        sk, ck = taylor(a)
-        sj, cj = taylor(b)
+        sk, ck = taylor_half(a)   # the tensor-core tiles' polynomials
+        sj, cj = taylor_half(b)
         sv = f32(f32(sk - sj) + fma(sk, cj, -f32(ck * sj)))
         mv = fma(ck, cj, fma(sk, sj, f32(ck + cj)))
         d = np.float64(a) - np.float64(b)
