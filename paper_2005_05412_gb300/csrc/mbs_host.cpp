@@ -57,6 +57,7 @@ int upload(const std::vector<double> &h, void **dptr, int prec) {
     e = cudaMemcpy(*dptr, h.data(), n * sizeof(double), cudaMemcpyHostToDevice);
   } else {
     std::vector<float> f(n);
+#pragma omp parallel for schedule(static) if (n > 65536)
     for (size_t i = 0; i < n; ++i) f[i] = (float)h[i];
     e = cudaMemcpy(*dptr, f.data(), n * sizeof(float), cudaMemcpyHostToDevice);
   }
@@ -448,7 +449,10 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
     for (int i = 0; i < K; ++i) d0_slot[sl * K + i] = x0[full_of(N, i)] + (q.yinit[full_of(N, i)] - q.yref[full_of(N, i)]);
   }
   int bad = 0;
-#pragma omp parallel for schedule(dynamic, 256) reduction(+ : bad)
+#pragma omp parallel reduction(+ : bad)
+  {
+  Step st;   // one per thread: its vectors keep their capacity from cell to cell
+#pragma omp for schedule(dynamic, 256)
   for (int m = 0; m < nx; ++m) {
     const int mt = dev->cell_mat[m];
     const int sl = s->qslot[mt];
@@ -460,7 +464,6 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
     const MatDesc &mm = dev->mats[mt];
     const QDesc &q = dev->qms[mm.qm];
     const double fd = dev->jitter[2 * m], fh = dev->jitter[2 * m + 1];
-    Step st;
     build_step(q, fh, dt, st);
     const double bp = (dt / (kEps0 * mm.eps_r)) / (1 + dt * mm.sigma / (2 * kEps0 * mm.eps_r));
     const double cpl = bp * mm.overlap * q.n3d * fd;
@@ -471,12 +474,15 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
       s->pcell[(size_t)(K * K + K + i) * ld + col] = cpl * st.g[i];
     }
     s->pcell[(size_t)(K * K + 2 * K) * ld + col] = cpl * st.g0;
-    std::vector<double> x0(N2, 0.0);
-    for (int i = 0; i < N2; ++i)
+    double x0[mbs::NMAX * mbs::NMAX];
+    for (int i = 0; i < N2; ++i) {
+      x0[i] = 0.0;
       for (int j = 0; j < N2; ++j) x0[i] += st.Ehm1[i * N2 + j] * q.yinit[j];
+    }
     for (int i = 0; i < K; ++i)
       s->Dinit[(size_t)i * ld + col] = x0[full_of(N, i)] + (q.yinit[full_of(N, i)] - q.yref[full_of(N, i)]);
     if (!std::isfinite(st.AK[0])) ++bad;
+  }
   }
   if (bad) return fail(MBS_E_NUMERIC, "non-finite per-cell propagator");
 

@@ -172,15 +172,20 @@ bool eigh_hq(int n, const cd *A, double *w, cd *V) {
   return true;
 }
 
-// exp(A) - I for a real n x n matrix, accurate relative to itself: scale by
-// 2^-s until ||A||_1 <= 1/4, sum the Taylor series without its leading
-// identity to order 20 (remainder < 1e-32 relative), and undo the scaling
-// with the squarings in the same form, exp(2B) - I = E (E + 2 I) for
-// E = exp(B) - I.  The step operators act on small deviations through
-// exp(L0 dt) - I, whose entries are ~|L0| dt; forming exp(L0 dt) first and
-// subtracting I would leave them with an absolute error of one ulp of 1 --
-// a systematic error repeated every step.
+// exp(A) - I for a real n x n matrix (n <= NMAX^2), accurate relative to
+// itself: scale by 2^-s until ||A||_1 <= 1/4, sum the Taylor series without
+// its leading identity until a term falls below 2^-70 of the largest entry
+// of the sum (at most order 20; with ||B|| <= 1/4 each further term is at
+// least 4 (k+1) times smaller, so the remainder stays below 2^-70 of the
+// sum's largest entry), and undo the scaling with the squarings in the same
+// form, exp(2B) - I = E (E + 2 I) for E = exp(B) - I.  The step operators
+// act on small deviations through exp(L0 dt) - I, whose entries are
+// ~|L0| dt; forming exp(L0 dt) first and subtracting I would leave them with
+// an absolute error of one ulp of 1 -- a systematic error repeated every
+// step.  Work arrays on the stack: the jittered media call this once per
+// cell.
 void expm1_taylor(int n, const double *A, double *E) {
+  constexpr int MX = mbs::NMAX * mbs::NMAX * mbs::NMAX * mbs::NMAX;
   double nrm = 0;
   for (int j = 0; j < n; ++j) {
     double s = 0;
@@ -197,17 +202,21 @@ void expm1_taylor(int n, const double *A, double *E) {
     ++sq;
   }
   const double sc = std::ldexp(1.0, -sq);
-  std::vector<double> B(n * n), term(n * n), t2(n * n);
+  double B[MX], term[MX], t2[MX];
   for (int i = 0; i < n * n; ++i) B[i] = term[i] = E[i] = A[i] * sc;
   for (int k = 2; k <= 20; ++k) {
-    rmatmul(n, term.data(), B.data(), t2.data());
+    rmatmul(n, term, B, t2);
+    double tmax = 0, emax = 0;
     for (int i = 0; i < n * n; ++i) {
       term[i] = t2[i] / k;
       E[i] += term[i];
+      tmax = std::max(tmax, std::fabs(term[i]));
+      emax = std::max(emax, std::fabs(E[i]));
     }
+    if (tmax <= 0x1p-70 * emax) break;
   }
   for (int k = 0; k < sq; ++k) {
-    rmatmul(n, E, E, t2.data());
+    rmatmul(n, E, E, t2);
     for (int i = 0; i < n * n; ++i) E[i] = t2[i] + 2.0 * E[i];
   }
 }
@@ -268,16 +277,19 @@ void y_to_herm(int N, const double *y, cd *X) {
 
 void build_step(const QDesc &q, double hfac, double dt, Step &s) {
   const int N = q.N, N2 = N * N, K = N2 - 1;
-  std::vector<double> M(N2 * N2), Mh(N2 * N2), Eh(N2 * N2), Em1(N2 * N2);
+  constexpr int MX = mbs::NMAX * mbs::NMAX * mbs::NMAX * mbs::NMAX, VX = mbs::NMAX * mbs::NMAX;
+  // work arrays on the stack; the Step's vectors keep their capacity when
+  // the caller reuses it (one call per cell for jittered media)
+  double M[MX], Mh[MX], Eh[MX], Em1[MX], MAh[MX], ay[VX], gf[VX];
   for (int i = 0; i < N2 * N2; ++i) M[i] = hfac * q.MH[i] + q.MD[i];
   for (int i = 0; i < N2 * N2; ++i) Mh[i] = 0.5 * dt * M[i];
   // exp(L0 dt/2) - I, and exp(L0 dt) - I = Eh (Eh + 2 I)
-  expm1_taylor(N2, Mh.data(), Eh.data());
-  rmatmul(N2, Eh.data(), Eh.data(), Em1.data());
+  expm1_taylor(N2, Mh, Eh);
+  rmatmul(N2, Eh, Eh, Em1);
   for (int i = 0; i < N2 * N2; ++i) Em1[i] += 2.0 * Eh[i];
-  s.Ah = Eh;
+  s.Ah.assign(Eh, Eh + N2 * N2);
   for (int i = 0; i < N2; ++i) s.Ah[i * N2 + i] += 1.0;
-  s.Ehm1 = Eh;
+  s.Ehm1.assign(Eh, Eh + N2 * N2);
   // deviation coordinates drop rho~_{N-1,N-1} = 1 - sum of the others:
   // (A - I)_ij = Em1[fi][fj] - Em1[fi][N-1] for population columns j
   s.AKm1.assign(K * K, 0.0);
@@ -289,15 +301,15 @@ void build_step(const QDesc &q, double hfac, double dt, Step &s) {
       s.AK[i * K + j] = s.AKm1[i * K + j] + (i == j ? 1.0 : 0.0);
     }
   // affine offset at the reference state: (A - I) yref
-  std::vector<double> ay(N2, 0.0);
-  for (int i = 0; i < N2; ++i)
+  for (int i = 0; i < N2; ++i) {
+    ay[i] = 0.0;
     for (int j = 0; j < N2; ++j) ay[i] += Em1[i * N2 + j] * q.yref[j];
+  }
   s.c.assign(K, 0.0);
   for (int i = 0; i < K; ++i) s.c[i] = ay[full_of(N, i)];
   // d_t P / n3D = tr(mu L0 exp(L0 dt/2) v) = sum_j lambda_j [M Ah y]_j
-  std::vector<double> MAh(N2 * N2);
-  rmatmul(N2, M.data(), s.Ah.data(), MAh.data());
-  std::vector<double> gf(N2, 0.0);
+  rmatmul(N2, M, s.Ah.data(), MAh);
+  for (int c = 0; c < N2; ++c) gf[c] = 0.0;
   for (int j = 0; j < N; ++j)
     for (int c = 0; c < N2; ++c) gf[c] += q.lambda[j] * MAh[j * N2 + c];
   s.g.assign(K, 0.0);
