@@ -47,6 +47,20 @@ void rmatmul(int n, const double *a, const double *b, double *c) {
     }
 }
 
+// the same for a size known at compile time (rows of b streamed into c)
+template <int n>
+static void rmatmul_n(const double *a, const double *b, double *c) {
+  for (int i = 0; i < n; ++i) {
+    double r[n];
+    for (int j = 0; j < n; ++j) r[j] = 0.0;
+    for (int k = 0; k < n; ++k) {
+      const double x = a[i * n + k];
+      for (int j = 0; j < n; ++j) r[j] += x * b[k * n + j];
+    }
+    for (int j = 0; j < n; ++j) c[i * n + j] = r[j];
+  }
+}
+
 // X^+ A X for n x n complex matrices
 std::vector<cd> conj_transform(int n, const std::vector<cd> &X, const cd *A) {
   std::vector<cd> t(n * n), xh(n * n), out(n * n);
@@ -173,19 +187,19 @@ bool eigh_hq(int n, const cd *A, double *w, cd *V) {
 }
 
 // exp(A) - I for a real n x n matrix (n <= NMAX^2), accurate relative to
-// itself: scale by 2^-s until ||A||_1 <= 1/4, sum the Taylor series without
-// its leading identity until a term falls below 2^-70 of the largest entry
-// of the sum (at most order 20; with ||B|| <= 1/4 each further term is at
-// least 4 (k+1) times smaller, so the remainder stays below 2^-70 of the
-// sum's largest entry), and undo the scaling with the squarings in the same
-// form, exp(2B) - I = E (E + 2 I) for E = exp(B) - I.  The step operators
-// act on small deviations through exp(L0 dt) - I, whose entries are
-// ~|L0| dt; forming exp(L0 dt) first and subtracting I would leave them with
-// an absolute error of one ulp of 1 -- a systematic error repeated every
-// step.  Work arrays on the stack: the jittered media call this once per
-// cell.
-void expm1_taylor(int n, const double *A, double *E) {
-  constexpr int MX = mbs::NMAX * mbs::NMAX * mbs::NMAX * mbs::NMAX;
+// itself: scale by 2^-s until ||A||_1 <= 1/4, evaluate the Taylor series
+// without its leading identity in nested (Horner) form,
+//   exp(B) - I = B (I + B/2 (I + B/3 (... (I + B/m)))),
+// with the smallest m whose truncation bound ||B||^m / (m + 1)! stays below
+// 2^-70 (at most 16 terms at ||B|| = 1/4), and undo the scaling with the
+// squarings in the same form, exp(2B) - I = E (E + 2 I) for
+// E = exp(B) - I.  The step operators act on small deviations through
+// exp(L0 dt) - I, whose entries are ~|L0| dt; forming exp(L0 dt) first and
+// subtracting I would leave them with an absolute error of one ulp of 1 --
+// a systematic error repeated every step.  Fixed sizes and work arrays on
+// the stack: the jittered media call this once per cell.
+template <int n>
+static void expm1_horner(const double *A, double *E) {
   double nrm = 0;
   for (int j = 0; j < n; ++j) {
     double s = 0;
@@ -202,23 +216,48 @@ void expm1_taylor(int n, const double *A, double *E) {
     ++sq;
   }
   const double sc = std::ldexp(1.0, -sq);
-  double B[MX], term[MX], t2[MX];
-  for (int i = 0; i < n * n; ++i) B[i] = term[i] = E[i] = A[i] * sc;
-  for (int k = 2; k <= 20; ++k) {
-    rmatmul(n, term, B, t2);
-    double tmax = 0, emax = 0;
-    for (int i = 0; i < n * n; ++i) {
-      term[i] = t2[i] / k;
-      E[i] += term[i];
-      tmax = std::max(tmax, std::fabs(term[i]));
-      emax = std::max(emax, std::fabs(E[i]));
-    }
-    if (tmax <= 0x1p-70 * emax) break;
+  int m = 1;
+  for (double bound = nrm / 2.0; m < 20 && bound > 0x1p-70; bound *= nrm / (m + 2)) ++m;
+  double B[n * n], P[n * n], T[n * n];
+  for (int i = 0; i < n * n; ++i) {
+    B[i] = A[i] * sc;
+    P[i] = B[i] / m;
+  }
+  for (int k = m - 1; k >= 1; --k) {
+    for (int i = 0; i < n; ++i) P[i * n + i] += 1.0;
+    rmatmul_n<n>(B, P, T);
+    for (int i = 0; i < n * n; ++i) P[i] = T[i] / k;
   }
   for (int k = 0; k < sq; ++k) {
-    rmatmul(n, E, E, t2);
-    for (int i = 0; i < n * n; ++i) E[i] = t2[i] + 2.0 * E[i];
+    rmatmul_n<n>(P, P, T);
+    for (int i = 0; i < n * n; ++i) P[i] = T[i] + 2.0 * P[i];
   }
+  for (int i = 0; i < n * n; ++i) E[i] = P[i];
+}
+
+// rmatmul for the Liouville-space sizes (N^2, N = 2..6) through the
+// fixed-size form
+static void rmatmul_liou(int n, const double *a, const double *b, double *c) {
+  switch (n) {
+    case 4: return rmatmul_n<4>(a, b, c);
+    case 9: return rmatmul_n<9>(a, b, c);
+    case 16: return rmatmul_n<16>(a, b, c);
+    case 25: return rmatmul_n<25>(a, b, c);
+    case 36: return rmatmul_n<36>(a, b, c);
+    default: return rmatmul(n, a, b, c);
+  }
+}
+
+void expm1_taylor(int n, const double *A, double *E) {
+  switch (n) {
+    case 4: return expm1_horner<4>(A, E);
+    case 9: return expm1_horner<9>(A, E);
+    case 16: return expm1_horner<16>(A, E);
+    case 25: return expm1_horner<25>(A, E);
+    case 36: return expm1_horner<36>(A, E);
+    default: break;
+  }
+  for (int i = 0; i < n * n; ++i) E[i] = std::nan("");   // not a Liouville-space size
 }
 
 // Solve A x = b (n x n, partial pivoting).  Returns the smallest |pivot|
@@ -285,7 +324,7 @@ void build_step(const QDesc &q, double hfac, double dt, Step &s) {
   for (int i = 0; i < N2 * N2; ++i) Mh[i] = 0.5 * dt * M[i];
   // exp(L0 dt/2) - I, and exp(L0 dt) - I = Eh (Eh + 2 I)
   expm1_taylor(N2, Mh, Eh);
-  rmatmul(N2, Eh, Eh, Em1);
+  rmatmul_liou(N2, Eh, Eh, Em1);
   for (int i = 0; i < N2 * N2; ++i) Em1[i] += 2.0 * Eh[i];
   s.Ah.assign(Eh, Eh + N2 * N2);
   for (int i = 0; i < N2; ++i) s.Ah[i * N2 + i] += 1.0;
@@ -308,7 +347,7 @@ void build_step(const QDesc &q, double hfac, double dt, Step &s) {
   s.c.assign(K, 0.0);
   for (int i = 0; i < K; ++i) s.c[i] = ay[full_of(N, i)];
   // d_t P / n3D = tr(mu L0 exp(L0 dt/2) v) = sum_j lambda_j [M Ah y]_j
-  rmatmul(N2, M, s.Ah.data(), MAh);
+  rmatmul_liou(N2, M, s.Ah.data(), MAh);
   for (int c = 0; c < N2; ++c) gf[c] = 0.0;
   for (int j = 0; j < N; ++j)
     for (int c = 0; c < N2; ++c) gf[c] += q.lambda[j] * MAh[j * N2 + c];
