@@ -1025,9 +1025,11 @@ __device__ __forceinline__ void tile_body(const Args &a, const int tile, long lo
         elh = s_x[(wib - 1) * 4 + 0];
         ell = s_x[(wib - 1) * 4 + 1];
       }
+      // no extra term: -0 (x + -0 == x for every x, so the addition drops
+      // out at compile time; x + +0 would not, as -0 + +0 == +0)
 #pragma unroll
       for (int j = R - 1; j >= 0; --j)
-        fld_axpy_diff_step<real>(H[j], Hl[j], ch[j], E[j], El[j], j ? E[j - 1] : elh, j ? El[j - 1] : ell, real(0));
+        fld_axpy_diff_step<real>(H[j], Hl[j], ch[j], E[j], El[j], j ? E[j - 1] : elh, j ? El[j - 1] : ell, real(-0.0));
     }
     if (any_src) {
       for (int s = 0; s < a.n_src; ++s) {

@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(128 * G, 4 / G)
         elh = s_x[(wib - 1) * 4 + 0];
         ell = s_x[(wib - 1) * 4 + 1];
       }
-      fld_axpy_diff<float, true>(H, Hl, ch, E, El, elh, ell, 0.0f);
+      fld_axpy_diff<float, true>(H, Hl, ch, E, El, elh, ell, -0.0f);   // -0: the extra addition drops out
     }
     if (any_src)
       for (int s = 0; s < a.n_src; ++s)
