@@ -353,8 +353,13 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
     return fail(MBS_E_INVALID, "0..%d probes", mbs::MAXPROBE);
   const int nx = dev->nx;
   const double dz = dev->dz;
-  double cmax = 0;
-  for (int m = 0; m < nx; ++m) cmax = std::max(cmax, light_speed(dev->mats[dev->cell_mat[m]]));
+  double cmax = 0;   // over the materials that some cell holds
+  {
+    std::vector<char> used(dev->mats.size(), 0);
+    for (int m = 0; m < nx; ++m) used[dev->cell_mat[m]] = 1;
+    for (size_t i = 0; i < used.size(); ++i)
+      if (used[i]) cmax = std::max(cmax, light_speed(dev->mats[i]));
+  }
   double dt;
   if (dt_or_0 > 0) {
     dt = dt_or_0;
@@ -545,6 +550,7 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
     const double bh = s->emc[dev->cell_mat[sr.cell] * 4 + 1];
     const double ch = h.face >= 0 ? s->emc[dev->cell_mat[h.face] * 4 + 2] : 0.0;
     auto S = [&](double t) { return sr.e0 * envelope(sr.shape, (t - sr.t0) / sr.tau) * std::sin(sr.omega * t + sr.phase); };
+#pragma omp parallel for schedule(static) if (nt > 16384)
     for (long long n = 0; n < nt; ++n) {
       const double tn = n * dt;
       if (sr.kind == MBS_SRC_HARD) {
