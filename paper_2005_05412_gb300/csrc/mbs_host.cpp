@@ -342,6 +342,24 @@ int mbs_device_propagators(mbs_device_t dev, int qm, double dt, double *lambda, 
   return MBS_OK;
 }
 
+// The structured two-level rows of one cell from its dense rows (A - I,
+// the offset c, the coupling w, w0): true and the 7 rows when A - I has the
+// optical-Bloch pattern (non-zero only at (0,0), (0,2), (1,1), (2,0), (2,2)),
+// the offset vanishes and the coupling has no (1) component and no constant.
+static bool bloch2_rows(const double *A, const double *c, const double *w, double w0, double *rows) {
+  double amax = 0, wmax = 0;
+  for (int r = 0; r < 9; ++r) amax = std::max(amax, std::fabs(A[r]));
+  for (int r = 0; r < 3; ++r) wmax = std::max(wmax, std::fabs(w[r]));
+  const double ta = 1e-13 * amax, tw = 1e-13 * wmax;
+  if (std::fabs(A[1]) > ta || std::fabs(A[3]) > ta || std::fabs(A[5]) > ta || std::fabs(A[7]) > ta ||
+      std::fabs(c[0]) > 1e-13 || std::fabs(c[1]) > 1e-13 || std::fabs(c[2]) > 1e-13 || std::fabs(w[1]) > tw ||
+      std::fabs(w0) > tw)
+    return false;
+  const double v[7] = {A[0], A[2], A[4], A[6], A[8], w[0], w[2]};
+  for (int r = 0; r < 7; ++r) rows[r] = v[r];
+  return true;
+}
+
 int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end, long long n_steps,
                  const mbs_source *src, int n_src, const mbs_probe *probes, int n_probes, mbs_scenario_t *out) {
   g_err.clear();
@@ -453,8 +471,12 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
       for (int j = 0; j < N2; ++j) x0[i] += steps[sl].Ehm1[i * N2 + j] * q.yinit[j];
     for (int i = 0; i < K; ++i) d0_slot[sl * K + i] = x0[full_of(N, i)] + (q.yinit[full_of(N, i)] - q.yref[full_of(N, i)]);
   }
-  int bad = 0;
-#pragma omp parallel reduction(+ : bad)
+  // structured two-level rows (see bloch2_rows): of jittered media formed in
+  // the per-cell loop below, of uniform media from their slots after it
+  const bool b2_try = N == 2 && s->n_slot > 0;
+  if (b2_try) s->pcell2.assign((size_t)7 * ld, 0.0);
+  int bad = 0, bad2 = 0;
+#pragma omp parallel reduction(+ : bad, bad2)
   {
   Step st;   // one per thread: its vectors keep their capacity from cell to cell
 #pragma omp for schedule(dynamic, 256)
@@ -479,6 +501,14 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
       s->pcell[(size_t)(K * K + K + i) * ld + col] = cpl * st.g[i];
     }
     s->pcell[(size_t)(K * K + 2 * K) * ld + col] = cpl * st.g0;
+    if (b2_try) {
+      const double w[3] = {cpl * st.g[0], cpl * st.g[1], cpl * st.g[2]};
+      double rows[7];
+      if (bloch2_rows(st.AKm1.data(), st.c.data(), w, cpl * st.g0, rows))
+        for (int r = 0; r < 7; ++r) s->pcell2[(size_t)r * ld + col] = rows[r];
+      else
+        ++bad2;
+    }
     double x0[mbs::NMAX * mbs::NMAX];
     for (int i = 0; i < N2; ++i) {
       x0[i] = 0.0;
@@ -491,41 +521,22 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
   }
   if (bad) return fail(MBS_E_NUMERIC, "non-finite per-cell propagator");
 
-  // structured two-level rows: every medium cell's step operator has the
-  // optical-Bloch pattern (A - I non-zero only at (0,0), (0,2), (1,1), (2,0),
-  // (2,2); no affine offset; no coupling through component 1)
-  if (N == 2 && s->n_slot > 0) {
+  if (b2_try && !s->has_pcell) {   // uniform media: one set of rows per slot
     const int stride = s->qstride;
-    auto val = [&](int m, int slot, int r) {   // dense row r of cell m
-      return s->has_pcell ? s->pcell[(size_t)r * ld + off + m] : s->qpar[(size_t)slot * stride + r];
-    };
-    s->pcell2.assign((size_t)7 * ld, 0.0);
-    int bad2 = 0;
-#pragma omp parallel for schedule(static) reduction(+ : bad2)
-    for (int m = 0; m < nx; ++m) {
-      const int sl = s->qslot[dev->cell_mat[m]];
-      if (sl < 0) continue;
-      double A[9], c[3], w[3];
-      for (int r = 0; r < 9; ++r) A[r] = val(m, sl, r);
-      for (int r = 0; r < 3; ++r) {
-        c[r] = val(m, sl, 9 + r);
-        w[r] = val(m, sl, 12 + r);
-      }
-      const double w0 = val(m, sl, 15);
-      double amax = 0, wmax = 0;
-      for (double x : A) amax = std::max(amax, std::fabs(x));
-      for (double x : w) wmax = std::max(wmax, std::fabs(x));
-      const double ta = 1e-13 * amax, tw = 1e-13 * wmax;
-      if (std::fabs(A[1]) > ta || std::fabs(A[3]) > ta || std::fabs(A[5]) > ta || std::fabs(A[7]) > ta ||
-          std::fabs(c[0]) > 1e-13 || std::fabs(c[1]) > 1e-13 || std::fabs(c[2]) > 1e-13 || std::fabs(w[1]) > tw ||
-          std::fabs(w0) > tw) {
-        ++bad2;
-        continue;
-      }
-      const size_t col = (size_t)off + m;
-      const double rows[7] = {A[0], A[2], A[4], A[6], A[8], w[0], w[2]};
-      for (int r = 0; r < 7; ++r) s->pcell2[(size_t)r * ld + col] = rows[r];
+    std::vector<double> srows((size_t)s->n_slot * 7);
+    for (int sl = 0; sl < s->n_slot; ++sl) {
+      const double *blk = &s->qpar[(size_t)sl * stride];
+      if (!bloch2_rows(blk, blk + 9, blk + 12, blk[15], &srows[(size_t)sl * 7])) ++bad2;
     }
+    if (bad2 == 0)
+#pragma omp parallel for schedule(static)
+      for (int m = 0; m < nx; ++m) {
+        const int sl = s->qslot[dev->cell_mat[m]];
+        if (sl < 0) continue;
+        for (int r = 0; r < 7; ++r) s->pcell2[(size_t)r * ld + off + m] = srows[(size_t)sl * 7 + r];
+      }
+  }
+  if (b2_try) {
     s->has_b2 = bad2 == 0;
     if (!s->has_b2) s->pcell2.clear();
   }
@@ -596,12 +607,13 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
   }
   // cells for the state check: probes plus a strided sample of media
   {
-    std::vector<int> med;
-    for (int m = 0; m < nx; ++m)
-      if (s->qslot[dev->cell_mat[m]] >= 0) med.push_back(m);
+    size_t n_med = 0;
+    for (int m = 0; m < nx; ++m) n_med += s->qslot[dev->cell_mat[m]] >= 0;
     const size_t want = 4096;
-    const size_t stride = std::max<size_t>(1, med.size() / want);
-    for (size_t i = 0; i < med.size(); i += stride) s->chk_cells.push_back(med[i]);
+    const size_t stride = std::max<size_t>(1, n_med / want);
+    size_t i = 0;   // index among the medium cells
+    for (int m = 0; m < nx; ++m)
+      if (s->qslot[dev->cell_mat[m]] >= 0 && i++ % stride == 0) s->chk_cells.push_back(m);
     for (int c : s->pr_cell) s->chk_cells.push_back(c);
   }
 

@@ -226,26 +226,14 @@ static void expm1_horner(const double *A, double *E) {
   for (int k = m - 1; k >= 1; --k) {
     for (int i = 0; i < n; ++i) P[i * n + i] += 1.0;
     rmatmul_n<n>(B, P, T);
-    for (int i = 0; i < n * n; ++i) P[i] = T[i] / k;
+    const double rk = 1.0 / k;   // one division per term (each product rounds once more)
+    for (int i = 0; i < n * n; ++i) P[i] = T[i] * rk;
   }
   for (int k = 0; k < sq; ++k) {
     rmatmul_n<n>(P, P, T);
     for (int i = 0; i < n * n; ++i) P[i] = T[i] + 2.0 * P[i];
   }
   for (int i = 0; i < n * n; ++i) E[i] = P[i];
-}
-
-// rmatmul for the Liouville-space sizes (N^2, N = 2..6) through the
-// fixed-size form
-static void rmatmul_liou(int n, const double *a, const double *b, double *c) {
-  switch (n) {
-    case 4: return rmatmul_n<4>(a, b, c);
-    case 9: return rmatmul_n<9>(a, b, c);
-    case 16: return rmatmul_n<16>(a, b, c);
-    case 25: return rmatmul_n<25>(a, b, c);
-    case 36: return rmatmul_n<36>(a, b, c);
-    default: return rmatmul(n, a, b, c);
-  }
 }
 
 void expm1_taylor(int n, const double *A, double *E) {
@@ -314,47 +302,67 @@ void y_to_herm(int N, const double *y, cd *X) {
 }
 
 
-void build_step(const QDesc &q, double hfac, double dt, Step &s) {
-  const int N = q.N, N2 = N * N, K = N2 - 1;
-  constexpr int MX = mbs::NMAX * mbs::NMAX * mbs::NMAX * mbs::NMAX, VX = mbs::NMAX * mbs::NMAX;
-  // work arrays on the stack; the Step's vectors keep their capacity when
-  // the caller reuses it (one call per cell for jittered media)
-  double M[MX], Mh[MX], Eh[MX], Em1[MX], MAh[MX], ay[VX], gf[VX];
-  for (int i = 0; i < N2 * N2; ++i) M[i] = hfac * q.MH[i] + q.MD[i];
-  for (int i = 0; i < N2 * N2; ++i) Mh[i] = 0.5 * dt * M[i];
+// One step's FP64 operators for a level count known at compile time (the
+// jittered media call this once per cell): the loops have fixed bounds and
+// the work arrays live on the stack; the Step's vectors keep their capacity
+// when the caller reuses it.
+template <int N>
+static void build_step_n(const QDesc &q, double hfac, double dt, Step &s) {
+  constexpr int N2 = N * N, K = N2 - 1;
+  auto fo = [](int i) { return i < N - 1 ? i : i + 1; };   // full coordinate of deviation component i
+  double M[N2 * N2], Mh[N2 * N2], Eh[N2 * N2], Em1[N2 * N2], MAh[N2 * N2], Ah[N2 * N2], ay[N2], gf[N2];
+  for (int i = 0; i < N2 * N2; ++i) {
+    M[i] = hfac * q.MH[i] + q.MD[i];
+    Mh[i] = 0.5 * dt * M[i];
+  }
   // exp(L0 dt/2) - I, and exp(L0 dt) - I = Eh (Eh + 2 I)
-  expm1_taylor(N2, Mh, Eh);
-  rmatmul_liou(N2, Eh, Eh, Em1);
-  for (int i = 0; i < N2 * N2; ++i) Em1[i] += 2.0 * Eh[i];
-  s.Ah.assign(Eh, Eh + N2 * N2);
-  for (int i = 0; i < N2; ++i) s.Ah[i * N2 + i] += 1.0;
+  expm1_horner<N2>(Mh, Eh);
+  rmatmul_n<N2>(Eh, Eh, Em1);
+  for (int i = 0; i < N2 * N2; ++i) {
+    Em1[i] += 2.0 * Eh[i];
+    Ah[i] = Eh[i];
+  }
+  for (int i = 0; i < N2; ++i) Ah[i * N2 + i] += 1.0;
+  s.Ah.assign(Ah, Ah + N2 * N2);
   s.Ehm1.assign(Eh, Eh + N2 * N2);
   // deviation coordinates drop rho~_{N-1,N-1} = 1 - sum of the others:
   // (A - I)_ij = Em1[fi][fj] - Em1[fi][N-1] for population columns j
-  s.AKm1.assign(K * K, 0.0);
-  s.AK.assign(K * K, 0.0);
+  s.AKm1.resize(K * K);
+  s.AK.resize(K * K);
   for (int i = 0; i < K; ++i)
     for (int j = 0; j < K; ++j) {
-      const int fi = full_of(N, i), fj = full_of(N, j);
-      s.AKm1[i * K + j] = Em1[fi * N2 + fj] - (j < N - 1 ? Em1[fi * N2 + N - 1] : 0.0);
-      s.AK[i * K + j] = s.AKm1[i * K + j] + (i == j ? 1.0 : 0.0);
+      const double v = Em1[fo(i) * N2 + fo(j)] - (j < N - 1 ? Em1[fo(i) * N2 + N - 1] : 0.0);
+      s.AKm1[i * K + j] = v;
+      s.AK[i * K + j] = v + (i == j ? 1.0 : 0.0);
     }
   // affine offset at the reference state: (A - I) yref
   for (int i = 0; i < N2; ++i) {
     ay[i] = 0.0;
     for (int j = 0; j < N2; ++j) ay[i] += Em1[i * N2 + j] * q.yref[j];
   }
-  s.c.assign(K, 0.0);
-  for (int i = 0; i < K; ++i) s.c[i] = ay[full_of(N, i)];
+  s.c.resize(K);
+  for (int i = 0; i < K; ++i) s.c[i] = ay[fo(i)];
   // d_t P / n3D = tr(mu L0 exp(L0 dt/2) v) = sum_j lambda_j [M Ah y]_j
-  rmatmul_liou(N2, M, s.Ah.data(), MAh);
+  rmatmul_n<N2>(M, Ah, MAh);
   for (int c = 0; c < N2; ++c) gf[c] = 0.0;
   for (int j = 0; j < N; ++j)
     for (int c = 0; c < N2; ++c) gf[c] += q.lambda[j] * MAh[j * N2 + c];
-  s.g.assign(K, 0.0);
-  for (int i = 0; i < K; ++i) s.g[i] = gf[full_of(N, i)] - (i < N - 1 ? gf[N - 1] : 0.0);
+  s.g.resize(K);
+  for (int i = 0; i < K; ++i) s.g[i] = gf[fo(i)] - (i < N - 1 ? gf[N - 1] : 0.0);
   s.g0 = 0;
   for (int c = 0; c < N2; ++c) s.g0 += gf[c] * q.yref[c];
+}
+
+void build_step(const QDesc &q, double hfac, double dt, Step &s) {
+  switch (q.N) {
+    case 2: return build_step_n<2>(q, hfac, dt, s);
+    case 3: return build_step_n<3>(q, hfac, dt, s);
+    case 4: return build_step_n<4>(q, hfac, dt, s);
+    case 5: return build_step_n<5>(q, hfac, dt, s);
+    case 6: return build_step_n<6>(q, hfac, dt, s);
+    default: break;
+  }
+  s = Step();   // no level count outside 2..6 reaches here (build_qdesc rejects it)
 }
 
 // Lab-basis functional rho_ab = h . y (real part if im == 0, imaginary part
