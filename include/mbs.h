@@ -149,7 +149,13 @@ typedef struct { int cell; int quantity; int i, j; } mbs_probe;
 /* Create a scenario on `dev`: builds the propagators for dt in FP64 on the
  * host, allocates the device state on the current CUDA device and uploads
  * it.  dt = dt_or_0 if > 0, else courant * dz / c_max (courant in (0, 1]);
- * dt must not exceed dz / c_max.  n_steps > 0 overrides t_end. */
+ * dt must not exceed dz / c_max.  n_steps > 0 overrides t_end.
+ * A two-level medium with per-cell jitter has one set of step operators per
+ * cell; those are formed in FP64 on the device (the host's arithmetic, one
+ * thread per cell) and only the jitter table is uploaded.  Setting the
+ * environment variable MBS_HOST_SETUP to a non-empty value other than "0"
+ * when this is called forms them on the host instead (for comparison).  A
+ * non-finite per-cell operator returns MBS_E_NUMERIC either way. */
 int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end, long long n_steps,
                  const mbs_source *src, int n_src,
                  const mbs_probe *probes, int n_probes,

@@ -17,9 +17,9 @@ NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 SOURCES_CU = ["mbs_tiled.cu", "mbs_tc.cu", "mbs_cells.cu", "mbs_plain.cu", "mbs_plain45.cu", "mbs_plain6.cu",
-              "mbs_static.cu", "mbs_peaks.cu"]
+              "mbs_static.cu", "mbs_peaks.cu", "mbs_setup_dev.cu"]
 SOURCES_CPP = ["mbs_setup.cpp", "mbs_host.cpp", "mbs_solve.cpp", "mbs_batch.cpp", "mbs_cells_host.cpp"]
-HEADERS = ["mbs_internal.h", "mbs_device.cuh", "mbs_host_internal.h"]
+HEADERS = ["mbs_internal.h", "mbs_device.cuh", "mbs_host_internal.h", "mbs_step_math.h", "mbs_setup_dev.h"]
 
 
 def _stale(target, deps):

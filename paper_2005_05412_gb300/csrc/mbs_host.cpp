@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #ifdef _OPENMP
@@ -19,6 +20,8 @@
 #endif
 
 #include "mbs_host_internal.h"
+#include "mbs_setup_dev.h"
+#include "mbs_step_math.h"
 
 namespace mbs_host {
 
@@ -130,11 +133,32 @@ int ensure_bundle(mbs_scenario_s *s, int prec) {
   for (int i = 0; i < 2; ++i)
     if ((e = cudaMalloc(&b.bprev[i], 4 * rb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc bprev");
   int rc;
-  if ((rc = upload(s->Dinit, &b.Dinit, prec))) return rc;
+  // rows formed on the device (jittered two-level media) in `prec`: a copy
+  // (FP64) or a conversion (FP32) of the scenario's FP64 rows
+  auto from_dev = [&](const double *src, size_t n, void **dst) -> int {
+    cudaError_t e2 = cudaMalloc(dst, n * rb);
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaMalloc");
+    if (prec == 0) {
+      e2 = cudaMemcpy(*dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice);
+      if (e2 != cudaSuccess) return cuda_fail(e2, "cudaMemcpy");
+    } else {
+      const int r2 = mbs::to_float(src, reinterpret_cast<float *>(*dst), n, nullptr);
+      if (r2) return cuda_fail((cudaError_t)r2, "FP32 copy of the per-cell rows");
+      if ((e2 = cudaStreamSynchronize(nullptr)) != cudaSuccess) return cuda_fail(e2, "FP32 copy of the per-cell rows");
+    }
+    return 0;
+  };
+  if (s->d_dinit64) {
+    if ((rc = from_dev(s->d_dinit64, (size_t)K * s->ld, &b.Dinit))) return rc;
+    if ((rc = from_dev(s->d_pcell64, (size_t)mbs::pc_rows(s->N) * s->ld, &b.pcell))) return rc;
+    if (s->has_b2 && (rc = from_dev(s->d_pcell2_64, (size_t)7 * s->ld, &b.pcell2))) return rc;
+  } else {
+    if ((rc = upload(s->Dinit, &b.Dinit, prec))) return rc;
+    if (s->has_pcell && (rc = upload(s->pcell, &b.pcell, prec))) return rc;
+    if (s->has_b2 && (rc = upload(s->pcell2, &b.pcell2, prec))) return rc;
+  }
   if ((rc = upload(s->emc, &b.emc, prec))) return rc;
   if ((rc = upload(s->qpar, &b.qpar, prec))) return rc;
-  if (s->has_pcell && (rc = upload(s->pcell, &b.pcell, prec))) return rc;
-  if (s->has_b2 && (rc = upload(s->pcell2, &b.pcell2, prec))) return rc;
   if (prec == 1) {
     // FP32 records of rho probes hold rho_ab - rho_ab(ref) (the constant term
     // is added in FP64 when the records are fetched), so that a population
@@ -229,6 +253,9 @@ void free_scenario(mbs_scenario_s *s) {
   cudaFree(s->d_zref);
   cudaFree(s->d_chk_min);
   cudaFree(s->d_chk_tr);
+  cudaFree(s->d_pcell64);
+  cudaFree(s->d_pcell2_64);
+  cudaFree(s->d_dinit64);
 }
 
 double light_speed(const MatDesc &m) { return 1.0 / std::sqrt(kEps0 * m.eps_r * kMu0 * m.mu_r); }
@@ -342,22 +369,63 @@ int mbs_device_propagators(mbs_device_t dev, int qm, double dt, double *lambda, 
   return MBS_OK;
 }
 
-// The structured two-level rows of one cell from its dense rows (A - I,
-// the offset c, the coupling w, w0): true and the 7 rows when A - I has the
-// optical-Bloch pattern (non-zero only at (0,0), (0,2), (1,1), (2,0), (2,2)),
-// the offset vanishes and the coupling has no (1) component and no constant.
-static bool bloch2_rows(const double *A, const double *c, const double *w, double w0, double *rows) {
-  double amax = 0, wmax = 0;
-  for (int r = 0; r < 9; ++r) amax = std::max(amax, std::fabs(A[r]));
-  for (int r = 0; r < 3; ++r) wmax = std::max(wmax, std::fabs(w[r]));
-  const double ta = 1e-13 * amax, tw = 1e-13 * wmax;
-  if (std::fabs(A[1]) > ta || std::fabs(A[3]) > ta || std::fabs(A[5]) > ta || std::fabs(A[7]) > ta ||
-      std::fabs(c[0]) > 1e-13 || std::fabs(c[1]) > 1e-13 || std::fabs(c[2]) > 1e-13 || std::fabs(w[1]) > tw ||
-      std::fabs(w0) > tw)
-    return false;
-  const double v[7] = {A[0], A[2], A[4], A[6], A[8], w[0], w[2]};
-  for (int r = 0; r < 7; ++r) rows[r] = v[r];
-  return true;
+// The per-cell operators of a jittered two-level medium on the device
+// (mbs_setup_dev.cu): the per-slot FP64 parts and the jitter table go up,
+// the FP64 rows stay on the device (the bundles copy or convert them), and
+// the two counts come back: a non-finite operator fails the scenario, a cell
+// without the optical-Bloch pattern turns the structured rows off.
+static int setup_on_device(mbs_scenario_s *s, const std::vector<int> &slot_mat, double dt) {
+  const mbs_device_s *dev = s->dev;
+  const int nx = dev->nx, ld = s->ld, K = s->K;
+  std::vector<mbs::SetupSlot2> slots(s->n_slot);
+  for (int sl = 0; sl < s->n_slot; ++sl) {
+    const MatDesc &mm = dev->mats[slot_mat[sl]];
+    const QDesc &q = dev->qms[mm.qm];
+    mbs::SetupSlot2 &o = slots[sl];
+    std::copy(q.MH.begin(), q.MH.end(), o.MH);
+    std::copy(q.MD.begin(), q.MD.end(), o.MD);
+    std::copy(q.yref.begin(), q.yref.end(), o.yref);
+    std::copy(q.yinit.begin(), q.yinit.end(), o.yinit);
+    std::copy(q.lambda.begin(), q.lambda.end(), o.lambda);
+    const double bp = (dt / (kEps0 * mm.eps_r)) / (1 + dt * mm.sigma / (2 * kEps0 * mm.eps_r));
+    o.cpl0 = bp * mm.overlap * q.n3d;
+  }
+  mbs::SetupSlot2 *d_slots = nullptr;
+  double *d_jit = nullptr;
+  int *d_counts = nullptr;
+  int rc = 0;
+  g_h2d = &s->h2d_bytes;
+  rc = upload_raw(slots, &d_slots);
+  if (!rc) rc = upload_raw(dev->jitter, &d_jit);
+  g_h2d = nullptr;
+  cudaError_t e = cudaSuccess;
+  const size_t pr = (size_t)mbs::pc_rows(s->N) * ld, p2 = (size_t)7 * ld, di = (size_t)K * ld;
+  if (!rc && ((e = cudaMalloc(&s->d_pcell64, pr * sizeof(double))) != cudaSuccess ||
+              (e = cudaMalloc(&s->d_pcell2_64, p2 * sizeof(double))) != cudaSuccess ||
+              (e = cudaMalloc(&s->d_dinit64, di * sizeof(double))) != cudaSuccess ||
+              (e = cudaMalloc(&d_counts, 2 * sizeof(int))) != cudaSuccess ||
+              (e = cudaMemset(s->d_pcell64, 0, pr * sizeof(double))) != cudaSuccess ||
+              (e = cudaMemset(s->d_pcell2_64, 0, p2 * sizeof(double))) != cudaSuccess ||
+              (e = cudaMemset(s->d_dinit64, 0, di * sizeof(double))) != cudaSuccess ||
+              (e = cudaMemset(d_counts, 0, 2 * sizeof(int))) != cudaSuccess))
+    rc = cuda_fail(e, "device setup buffers");
+  int counts[2] = {0, 0};
+  if (!rc && (rc = mbs::setup_cells2(d_slots, s->d_mat, s->d_qslot, d_jit, nx, s->off, ld, dt, s->d_pcell64,
+                                     s->d_pcell2_64, s->d_dinit64, d_counts, nullptr)))
+    rc = cuda_fail((cudaError_t)rc, "device setup");
+  if (!rc && (e = cudaMemcpy(counts, d_counts, sizeof(counts), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    rc = cuda_fail(e, "device setup");
+  cudaFree(d_slots);
+  cudaFree(d_jit);
+  cudaFree(d_counts);
+  if (rc) return rc;
+  if (counts[0]) return fail(MBS_E_NUMERIC, "non-finite per-cell propagator");
+  s->has_b2 = counts[1] == 0;
+  if (!s->has_b2) {
+    cudaFree(s->d_pcell2_64);
+    s->d_pcell2_64 = nullptr;
+  }
+  return 0;
 }
 
 int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end, long long n_steps,
@@ -457,11 +525,17 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
     mbs::tc_weight_table(N, s->qpar.data(), s->tcw.data());
   }
 
-  // per-cell state and (jittered media) per-cell step operators
+  // per-cell state and (jittered media) per-cell step operators; those of
+  // jittered two-level media are formed on the device (mbs_setup_dev.cu) at
+  // the end, unless MBS_HOST_SETUP is set to a non-empty value other than 0
   const int ld = s->ld, off = s->off;
-  s->Dinit.assign((size_t)K * ld, 0.0);
   s->has_pcell = !dev->jitter.empty() && s->n_slot > 0;
-  if (s->has_pcell) s->pcell.assign((size_t)mbs::pc_rows(N) * ld, 0.0);
+  const char *hs = std::getenv("MBS_HOST_SETUP");
+  const bool dev_setup = N == 2 && s->has_pcell && !(hs && hs[0] && std::strcmp(hs, "0") != 0);
+  if (!dev_setup) {
+    s->Dinit.assign((size_t)K * ld, 0.0);
+    if (s->has_pcell) s->pcell.assign((size_t)mbs::pc_rows(N) * ld, 0.0);
+  }
   std::vector<double> d0_slot((size_t)std::max(1, s->n_slot) * K, 0.0);
   for (int sl = 0; sl < s->n_slot; ++sl) {
     const QDesc &q = dev->qms[dev->mats[slot_mat[sl]].qm];
@@ -473,11 +547,11 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
   }
   // structured two-level rows (see bloch2_rows): of jittered media formed in
   // the per-cell loop below, of uniform media from their slots after it
-  const bool b2_try = N == 2 && s->n_slot > 0;
+  const bool b2_try = N == 2 && s->n_slot > 0 && !dev_setup;
   if (b2_try) s->pcell2.assign((size_t)7 * ld, 0.0);
   int bad = 0, bad2 = 0;
-#pragma omp parallel reduction(+ : bad, bad2)
-  {
+#pragma omp parallel reduction(+ : bad, bad2) if (!dev_setup)
+  if (!dev_setup) {
   Step st;   // one per thread: its vectors keep their capacity from cell to cell
 #pragma omp for schedule(dynamic, 256)
   for (int m = 0; m < nx; ++m) {
@@ -504,7 +578,7 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
     if (b2_try) {
       const double w[3] = {cpl * st.g[0], cpl * st.g[1], cpl * st.g[2]};
       double rows[7];
-      if (bloch2_rows(st.AKm1.data(), st.c.data(), w, cpl * st.g0, rows))
+      if (mbs_math::bloch2_rows(st.AKm1.data(), st.c.data(), w, cpl * st.g0, rows))
         for (int r = 0; r < 7; ++r) s->pcell2[(size_t)r * ld + col] = rows[r];
       else
         ++bad2;
@@ -526,7 +600,7 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
     std::vector<double> srows((size_t)s->n_slot * 7);
     for (int sl = 0; sl < s->n_slot; ++sl) {
       const double *blk = &s->qpar[(size_t)sl * stride];
-      if (!bloch2_rows(blk, blk + 9, blk + 12, blk[15], &srows[(size_t)sl * 7])) ++bad2;
+      if (!mbs_math::bloch2_rows(blk, blk + 9, blk + 12, blk[15], &srows[(size_t)sl * 7])) ++bad2;
     }
     if (bad2 == 0)
 #pragma omp parallel for schedule(static)
@@ -632,6 +706,10 @@ int mbs_scenario(mbs_device_t dev, double dt_or_0, double courant, double t_end,
     return rc;
   }
   g_h2d = nullptr;
+  if (dev_setup && (rc = setup_on_device(s.get(), slot_mat, dt))) {
+    free_scenario(s.get());
+    return rc;
+  }
   const size_t nchk = std::max<size_t>(1, s->chk_cells.size());
   if ((e = cudaMalloc(&s->d_flags, 4 * sizeof(int))) != cudaSuccess ||
       (e = cudaMalloc(&s->d_chk_min, nchk * sizeof(double))) != cudaSuccess ||

@@ -129,6 +129,9 @@ struct mbs_scenario_s {
   std::vector<mbs_host::SrcHost> src;
   double kmur_l = 0, kmur_r = 0;
   bool has_pcell = false;
+  // jittered two-level media set up on the device: the FP64 per-cell rows
+  // ([pc_rows][ld], [7][ld], [3][ld]); the bundles copy or convert them
+  double *d_pcell64 = nullptr, *d_pcell2_64 = nullptr, *d_dinit64 = nullptr;
   // device
   uint8_t *d_mat = nullptr;
   int *d_qslot = nullptr, *d_pr_cell = nullptr, *d_pr_q = nullptr, *d_flags = nullptr, *d_chk_cells = nullptr;

@@ -26,6 +26,7 @@
 #endif
 
 #include "mbs_host_internal.h"
+#include "mbs_step_math.h"
 
 namespace mbs_host {
 
@@ -45,20 +46,6 @@ void rmatmul(int n, const double *a, const double *b, double *c) {
       for (int k = 0; k < n; ++k) s += a[i * n + k] * b[k * n + j];
       c[i * n + j] = s;
     }
-}
-
-// the same for a size known at compile time (rows of b streamed into c)
-template <int n>
-static void rmatmul_n(const double *a, const double *b, double *c) {
-  for (int i = 0; i < n; ++i) {
-    double r[n];
-    for (int j = 0; j < n; ++j) r[j] = 0.0;
-    for (int k = 0; k < n; ++k) {
-      const double x = a[i * n + k];
-      for (int j = 0; j < n; ++j) r[j] += x * b[k * n + j];
-    }
-    for (int j = 0; j < n; ++j) c[i * n + j] = r[j];
-  }
 }
 
 // X^+ A X for n x n complex matrices
@@ -186,63 +173,16 @@ bool eigh_hq(int n, const cd *A, double *w, cd *V) {
   return true;
 }
 
-// exp(A) - I for a real n x n matrix (n <= NMAX^2), accurate relative to
-// itself: scale by 2^-s until ||A||_1 <= 1/4, evaluate the Taylor series
-// without its leading identity in nested (Horner) form,
-//   exp(B) - I = B (I + B/2 (I + B/3 (... (I + B/m)))),
-// with the smallest m whose truncation bound ||B||^m / (m + 1)! stays below
-// 2^-70 (at most 16 terms at ||B|| = 1/4), and undo the scaling with the
-// squarings in the same form, exp(2B) - I = E (E + 2 I) for
-// E = exp(B) - I.  The step operators act on small deviations through
-// exp(L0 dt) - I, whose entries are ~|L0| dt; forming exp(L0 dt) first and
-// subtracting I would leave them with an absolute error of one ulp of 1 --
-// a systematic error repeated every step.  Fixed sizes and work arrays on
-// the stack: the jittered media call this once per cell.
-template <int n>
-static void expm1_horner(const double *A, double *E) {
-  double nrm = 0;
-  for (int j = 0; j < n; ++j) {
-    double s = 0;
-    for (int i = 0; i < n; ++i) s += std::fabs(A[i * n + j]);
-    nrm = std::max(nrm, s);
-  }
-  if (!std::isfinite(nrm)) {
-    for (int i = 0; i < n * n; ++i) E[i] = std::nan("");
-    return;
-  }
-  int sq = 0;
-  while (nrm > 0.25) {
-    nrm *= 0.5;
-    ++sq;
-  }
-  const double sc = std::ldexp(1.0, -sq);
-  int m = 1;
-  for (double bound = nrm / 2.0; m < 20 && bound > 0x1p-70; bound *= nrm / (m + 2)) ++m;
-  double B[n * n], P[n * n], T[n * n];
-  for (int i = 0; i < n * n; ++i) {
-    B[i] = A[i] * sc;
-    P[i] = B[i] / m;
-  }
-  for (int k = m - 1; k >= 1; --k) {
-    for (int i = 0; i < n; ++i) P[i * n + i] += 1.0;
-    rmatmul_n<n>(B, P, T);
-    const double rk = 1.0 / k;   // one division per term (each product rounds once more)
-    for (int i = 0; i < n * n; ++i) P[i] = T[i] * rk;
-  }
-  for (int k = 0; k < sq; ++k) {
-    rmatmul_n<n>(P, P, T);
-    for (int i = 0; i < n * n; ++i) P[i] = T[i] + 2.0 * P[i];
-  }
-  for (int i = 0; i < n * n; ++i) E[i] = P[i];
-}
-
+// exp(A) - I for the Liouville-space sizes N^2 (N = 2..6): mbs_math::expm1_horner
+// (mbs_step_math.h: scaling, nested Taylor series without the identity,
+// squarings in the same form)
 void expm1_taylor(int n, const double *A, double *E) {
   switch (n) {
-    case 4: return expm1_horner<4>(A, E);
-    case 9: return expm1_horner<9>(A, E);
-    case 16: return expm1_horner<16>(A, E);
-    case 25: return expm1_horner<25>(A, E);
-    case 36: return expm1_horner<36>(A, E);
+    case 4: return mbs_math::expm1_horner<4>(A, E);
+    case 9: return mbs_math::expm1_horner<9>(A, E);
+    case 16: return mbs_math::expm1_horner<16>(A, E);
+    case 25: return mbs_math::expm1_horner<25>(A, E);
+    case 36: return mbs_math::expm1_horner<36>(A, E);
     default: break;
   }
   for (int i = 0; i < n * n; ++i) E[i] = std::nan("");   // not a Liouville-space size
@@ -302,55 +242,23 @@ void y_to_herm(int N, const double *y, cd *X) {
 }
 
 
-// One step's FP64 operators for a level count known at compile time (the
-// jittered media call this once per cell): the loops have fixed bounds and
-// the work arrays live on the stack; the Step's vectors keep their capacity
-// when the caller reuses it.
+// One step's FP64 operators for a level count known at compile time
+// (mbs_math::step_ops, the arithmetic the device setup of jittered two-level
+// media runs too); the Step's vectors keep their capacity when the caller
+// reuses it (one call per cell for jittered media).
 template <int N>
 static void build_step_n(const QDesc &q, double hfac, double dt, Step &s) {
   constexpr int N2 = N * N, K = N2 - 1;
-  auto fo = [](int i) { return i < N - 1 ? i : i + 1; };   // full coordinate of deviation component i
-  double M[N2 * N2], Mh[N2 * N2], Eh[N2 * N2], Em1[N2 * N2], MAh[N2 * N2], Ah[N2 * N2], ay[N2], gf[N2];
-  for (int i = 0; i < N2 * N2; ++i) {
-    M[i] = hfac * q.MH[i] + q.MD[i];
-    Mh[i] = 0.5 * dt * M[i];
-  }
-  // exp(L0 dt/2) - I, and exp(L0 dt) - I = Eh (Eh + 2 I)
-  expm1_horner<N2>(Mh, Eh);
-  rmatmul_n<N2>(Eh, Eh, Em1);
-  for (int i = 0; i < N2 * N2; ++i) {
-    Em1[i] += 2.0 * Eh[i];
-    Ah[i] = Eh[i];
-  }
-  for (int i = 0; i < N2; ++i) Ah[i * N2 + i] += 1.0;
-  s.Ah.assign(Ah, Ah + N2 * N2);
-  s.Ehm1.assign(Eh, Eh + N2 * N2);
-  // deviation coordinates drop rho~_{N-1,N-1} = 1 - sum of the others:
-  // (A - I)_ij = Em1[fi][fj] - Em1[fi][N-1] for population columns j
-  s.AKm1.resize(K * K);
-  s.AK.resize(K * K);
-  for (int i = 0; i < K; ++i)
-    for (int j = 0; j < K; ++j) {
-      const double v = Em1[fo(i) * N2 + fo(j)] - (j < N - 1 ? Em1[fo(i) * N2 + N - 1] : 0.0);
-      s.AKm1[i * K + j] = v;
-      s.AK[i * K + j] = v + (i == j ? 1.0 : 0.0);
-    }
-  // affine offset at the reference state: (A - I) yref
-  for (int i = 0; i < N2; ++i) {
-    ay[i] = 0.0;
-    for (int j = 0; j < N2; ++j) ay[i] += Em1[i * N2 + j] * q.yref[j];
-  }
-  s.c.resize(K);
-  for (int i = 0; i < K; ++i) s.c[i] = ay[fo(i)];
-  // d_t P / n3D = tr(mu L0 exp(L0 dt/2) v) = sum_j lambda_j [M Ah y]_j
-  rmatmul_n<N2>(M, Ah, MAh);
-  for (int c = 0; c < N2; ++c) gf[c] = 0.0;
-  for (int j = 0; j < N; ++j)
-    for (int c = 0; c < N2; ++c) gf[c] += q.lambda[j] * MAh[j * N2 + c];
-  s.g.resize(K);
-  for (int i = 0; i < K; ++i) s.g[i] = gf[fo(i)] - (i < N - 1 ? gf[N - 1] : 0.0);
-  s.g0 = 0;
-  for (int c = 0; c < N2; ++c) s.g0 += gf[c] * q.yref[c];
+  mbs_math::StepOps<N> o;
+  mbs_math::step_ops<N>(q.MH.data(), q.MD.data(), q.yref.data(), q.lambda.data(), hfac, dt, o);
+  s.Ah.assign(o.Ah, o.Ah + N2 * N2);
+  s.Ehm1.assign(o.Ehm1, o.Ehm1 + N2 * N2);
+  s.AKm1.assign(o.AKm1, o.AKm1 + K * K);
+  s.AK.assign(o.AKm1, o.AKm1 + K * K);
+  for (int i = 0; i < K; ++i) s.AK[i * K + i] += 1.0;
+  s.c.assign(o.c, o.c + K);
+  s.g.assign(o.g, o.g + K);
+  s.g0 = o.g0;
 }
 
 void build_step(const QDesc &q, double hfac, double dt, Step &s) {
