@@ -78,6 +78,11 @@ __global__ void __launch_bounds__(128, REG ? 4 : 1) k_cells(const CellsArgs a, l
   const real amp = reinterpret_cast<const real *>(a.amp)[s];
   const real *tab = reinterpret_cast<const real *>(a.tab) + (size_t)a.tab_id[s] * a.tab_stride;
   real *rec = reinterpret_cast<real *>(a.rec);
+  // step n records when (n + 1) % every == 0, into record (n + 1) / every - 1:
+  // the phase and quotient of n + 1 are carried from step to step (no
+  // 64-bit division in the loop)
+  long long q = (n0 + 1) / a.every;
+  int ph = (int)((n0 + 1) % a.every);
 #pragma unroll 1
   for (int t = 0; t < nsteps; ++t) {
     const long long n = n0 + t;
@@ -88,8 +93,8 @@ __global__ void __launch_bounds__(128, REG ? 4 : 1) k_cells(const CellsArgs a, l
       bloch_step<real, N, KAHAN>(qr, e, d, cc, u);
     else
       bloch_step<real, N, KAHAN>(qc, e, d, cc, u);
-    if ((n + 1) % a.every == 0) {
-      const long long r = (n + 1) / a.every - 1;
+    if (ph == 0) {
+      const long long r = q - 1;
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         real v = pop[(size_t)(k * (K + 1) + K) * a.n_sys];
@@ -97,6 +102,10 @@ __global__ void __launch_bounds__(128, REG ? 4 : 1) k_cells(const CellsArgs a, l
         for (int i = 0; i < K; ++i) v += pop[(size_t)(k * (K + 1) + i) * a.n_sys] * u[i];
         rec[((size_t)r * N + k) * a.n_sys + s] = v;
       }
+    }
+    if (++ph == a.every) {
+      ph = 0;
+      ++q;
     }
   }
 #pragma unroll
