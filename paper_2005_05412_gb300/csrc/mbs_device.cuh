@@ -46,21 +46,6 @@ static __device__ __forceinline__ void sincos_m1_wide(float x, float &s, float &
   cm1 = c - 1.0f;
 }
 
-// sin x and cos x - 1 by their Taylor polynomials (accurate for |x| <= 1/2)
-__device__ __forceinline__ void sincos_m1_taylor(float x, float &s, float &cm1) {
-  const float t = x * x;
-  float ps = fmaf(t, 1.0f / 362880.0f, -1.0f / 5040.0f);
-  ps = fmaf(t, ps, 1.0f / 120.0f);
-  ps = fmaf(t, ps, -1.0f / 6.0f);
-  ps = fmaf(t, ps, 1.0f);
-  s = x * ps;
-  float pc = fmaf(t, -1.0f / 3628800.0f, 1.0f / 40320.0f);
-  pc = fmaf(t, pc, -1.0f / 720.0f);
-  pc = fmaf(t, pc, 1.0f / 24.0f);
-  pc = fmaf(t, pc, -0.5f);
-  cm1 = t * pc;
-}
-
 // |x| > 1/2 in the tensor-core tiles: out of line, so that the common path
 // carries no library code; (sin x, cos x - 1) returned by value, so that the caller's
 // results stay in registers
@@ -70,10 +55,11 @@ static __device__ __noinline__ float2 sincos_m1_far(float x) {
   return r;
 }
 
-// The same polynomials two orders shorter (sin x to x^7, cos x - 1 to
-// x^8), for angles known to satisfy |x| <= 1/2: the alternating series'
-// first omitted terms, x^9/9! <= 5.4e-9 and x^10/10! <= 2.7e-10, stay below
-// half an ulp of sin x and of cos x - 1 on that range.
+// sin x and cos x - 1 by their Taylor polynomials to x^7 and x^8, for
+// angles known to satisfy |x| <= 1/2 (cos x - 1 never forms 1 - 1): the
+// alternating series' first omitted terms, x^9/9! <= 5.4e-9 and
+// x^10/10! <= 2.7e-10, stay below half an ulp of sin x and of cos x - 1 on
+// that range.
 __device__ __forceinline__ void sincos_m1_taylor_half(float x, float &s, float &cm1) {
   const float t = x * x;
   float ps = fmaf(t, -1.0f / 5040.0f, 1.0f / 120.0f);
@@ -86,9 +72,10 @@ __device__ __forceinline__ void sincos_m1_taylor_half(float x, float &s, float &
   cm1 = t * pc;
 }
 
-// sin x and cos x - 1 for any x
+// sin x and cos x - 1 for any x: the shorter polynomials within 1/2, the
+// library routine beyond
 __device__ __forceinline__ void sincos_m1(float x, float &s, float &cm1) {
-  sincos_m1_taylor(x, s, cm1);
+  sincos_m1_taylor_half(x, s, cm1);
   if (fabsf(x) > 0.5f) sincos_m1_wide(x, s, cm1);
 }
 

@@ -3,20 +3,16 @@
 The rotation exp(-i mu E dt / hbar) turns each coherence pair (j, k) of the
 dipole eigenbasis by theta_jk = (lambda_j - lambda_k) E dt / hbar (Sec. 2.2).
 The kernels form sin theta and cos theta - 1 (never 1 - 1) by Taylor
-polynomials up to x^9 and x^10 while |theta| <= 1/2 (a warp vote sends
-larger angles to the library routine), and the tensor-core tiles derive the
-pairs (j, k), j > 0, from theta_0k and theta_0j by the angle-difference
-identities written in sin and cos - 1.  In FP32 with fused multiply-adds
-(emulated: each fma rounded once from exact float64 products):
+polynomials to x^7 and x^8 while |theta| <= 1/2; larger angles go to the
+library routine (per angle, or for a whole warp after a vote in the
+two-level tiles), and the tensor-core tiles derive the pairs (j, k), j > 0,
+from theta_0k and theta_0j by the angle-difference identities written in
+sin and cos - 1.  In FP32 with fused multiply-adds (emulated: each fma
+rounded once from exact float64 products):
 
 * the polynomials hold sin x to 2 ulp and cos x - 1 to 3 ulp of the result
-  on |x| <= 1/2, and still on |x| <= 1: the guard's threshold keeps a factor
-  of 2 in hand (beyond |x| ~ 1.2 the truncated series fails);
-* the shorter polynomials (sin x to x^7, cos x - 1 to x^8) that the
-  two-level tiles take once a warp vote has shown every |x| <= 1/2, and the
-  tensor-core tiles for every angle within 1/2 (the library routine replaces
-  the others), hold the same 2 and 3 ulp there (the omitted terms are below
-  half an ulp), and fail beyond |x| ~ 1, which is what the guards are for;
+  on |x| <= 1/2 (the omitted terms are below half an ulp there), and fail
+  beyond |x| ~ 1, which is what the guards are for;
 * the identities reproduce sin and cos - 1 of the difference to 3 x 2^-24
   absolute, the order of rounding the difference angle itself in FP32
   (the rotation's entries are of order 1), and a wrong sign in either
@@ -29,22 +25,6 @@ f32 = np.float32
 
 def fma(a, b, c):
     return f32(np.float64(a) * np.float64(b) + np.float64(c))
-
-
-def taylor(x):
-    x = f32(x)
-    t = f32(x * x)
-    ps = fma(t, f32(1.0 / 362880.0), f32(-1.0 / 5040.0))
-    ps = fma(t, ps, f32(1.0 / 120.0))
-    ps = fma(t, ps, f32(-1.0 / 6.0))
-    ps = fma(t, ps, f32(1.0))
-    s = f32(x * ps)
-    pc = fma(t, f32(-1.0 / 3628800.0), f32(1.0 / 40320.0))
-    pc = fma(t, pc, f32(-1.0 / 720.0))
-    pc = fma(t, pc, f32(1.0 / 24.0))
-    pc = fma(t, pc, f32(-0.5))
-    cm1 = f32(t * pc)
-    return s, cm1
 
 
 def taylor_half(x):
@@ -66,21 +46,6 @@ def ulp(v):
 
 def cosm1(x):
     return -2.0 * np.sin(x / 2.0) ** 2
-
-
-def test_taylor_sin_and_cos_minus_one_on_the_guarded_range():
-    rng = np.random.default_rng(5)
-    xs = np.concatenate([rng.uniform(-1.0, 1.0, 20_000), np.geomspace(1e-12, 1.0, 2_000),
-                         -np.geomspace(1e-12, 1.0, 2_000), [0.5, -0.5, 1.0, -1.0]]).astype(np.float32)
-    es, ec = 0.0, 0.0
-    for x in xs:
-        s, c = taylor(x)
-        xd = np.float64(x)
-        es = max(es, abs(np.float64(s) - np.sin(xd)) / ulp(np.sin(xd)))
-        if xd != 0.0:
-            ec = max(ec, abs(np.float64(c) - cosm1(xd)) / ulp(cosm1(xd)))
-    assert es <= 2.0, es
-    assert ec <= 3.0, ec
 
 
 def test_angle_difference_identities():
